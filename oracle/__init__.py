@@ -1,0 +1,236 @@
+"""CPU oracle for the batched tau-leaping / SSA engine.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and
+the benchmark's CPU-baseline leg, never by the engine.  It shares no code
+with the CUDA path.
+
+Contents
+  tauleap_oracle.c  the algorithm in plain C (FP64, canonical operation order)
+  cme.py            exact transient law of tiny closed systems (Chemical
+                    Master Equation on a truncated state space)
+  rre.py            reaction-rate equations (the deterministic mean-field
+                    model) integrated with a library ODE solver
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MODE_TAU_LEAP = 0
+MODE_EXACT_SSA = 1
+STATUS_NAMES = {0: "OK", 1: "STEP_LIMIT", 2: "OVERFLOW", 3: "REJECT_LIMIT"}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32),
+        ("n_c", ctypes.c_int32),
+        ("eps", ctypes.c_double),
+        ("ssa_factor", ctypes.c_double),
+        ("ssa_block", ctypes.c_int32),
+        ("max_halvings", ctypes.c_int32),
+        ("max_attempts", ctypes.c_int64),
+    ]
+
+
+STATS_DTYPE = np.dtype([
+    ("status", np.int32), ("reserved", np.int32), ("leaps", np.int64), ("rejected", np.int64),
+    ("ssa_steps", np.int64), ("firings", np.int64), ("attempts", np.int64), ("t_final", np.float64),
+])
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.oracle_philox4x32_10.restype = None
+        L.oracle_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        L.oracle_u01.restype = ctypes.c_double
+        L.oracle_log.argtypes = [ctypes.c_double]
+        L.oracle_log.restype = ctypes.c_double
+        L.oracle_exp.argtypes = [ctypes.c_double]
+        L.oracle_exp.restype = ctypes.c_double
+        L.oracle_lnfact.argtypes = [ctypes.c_int64]
+        L.oracle_lnfact.restype = ctypes.c_double
+        L.oracle_poisson.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_uint32, ctypes.c_uint32]
+        L.oracle_poisson.restype = ctypes.c_int64
+        for name in ("oracle_log_array", "oracle_exp_array"):
+            getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+            getattr(L, name).restype = None
+        L.oracle_lnfact_array.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+        L.oracle_lnfact_array.restype = None
+        L.oracle_poisson_array.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.c_void_p]
+        L.oracle_poisson_array.restype = None
+        L.oracle_canon_sum.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        L.oracle_canon_sum.restype = ctypes.c_double
+        L.oracle_canon_select.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double]
+        L.oracle_canon_select.restype = ctypes.c_int32
+        L.oracle_leap_quantities.argtypes = [ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 8 + [
+            ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_leap_quantities.restype = ctypes.c_int
+        L.oracle_num_threads.argtypes = []
+        L.oracle_num_threads.restype = ctypes.c_int
+        vp = ctypes.c_void_p
+        L.oracle_simulate.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp,
+            ctypes.c_int64, vp, ctypes.c_int64, vp, vp, ctypes.c_double, vp, ctypes.c_int32,
+            ctypes.c_uint64, ctypes.POINTER(Opts), vp, vp, ctypes.c_int]
+        L.oracle_simulate.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def philox(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def u01(w0, w1):
+    return lib().oracle_u01(w0, w1)
+
+
+def log(x):
+    return lib().oracle_log(float(x))
+
+
+def exp(x):
+    return lib().oracle_exp(float(x))
+
+
+def lnfact(k):
+    return lib().oracle_lnfact(int(k))
+
+
+def poisson(lam, seed, sim, attempt, j):
+    return lib().oracle_poisson(float(lam), int(seed), int(sim), int(attempt), int(j))
+
+
+def log_array(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    lib().oracle_log_array(_ptr(x), _ptr(y), x.size)
+    return y
+
+
+def exp_array(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    lib().oracle_exp_array(_ptr(x), _ptr(y), x.size)
+    return y
+
+
+def lnfact_array(k):
+    k = np.ascontiguousarray(k, dtype=np.int64)
+    y = np.empty(k.shape, dtype=np.float64)
+    lib().oracle_lnfact_array(_ptr(k), _ptr(y), k.size)
+    return y
+
+
+def poisson_array(lam, n, seed=0):
+    """n draws of Poisson(lam); draw i uses simulation index i (attempt 1, reaction 0)."""
+    out = np.empty(int(n), dtype=np.int64)
+    lib().oracle_poisson_array(float(lam), int(seed), int(n), _ptr(out))
+    return out
+
+
+def canon_sum(v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return lib().oracle_canon_sum(_ptr(v), v.size)
+
+
+def canon_select(v, u):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return int(lib().oracle_canon_select(_ptr(v), v.size, float(u)))
+
+
+def leap_quantities(network, c, x, opts=None):
+    """Propensities, critical flags, a0, a0c and tau' for one state."""
+    csr = network.csr()
+    N, M = network.n_species, network.n_reactions
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    a = np.empty(M, dtype=np.float64)
+    crit = np.empty(M, dtype=np.int32)
+    sc = np.empty(3, dtype=np.float64)
+    o = opts if opts is not None else default_opts()
+    rc = lib().oracle_leap_quantities(
+        N, M, _ptr(csr["react_ptr"]), _ptr(csr["react_species"]), _ptr(csr["react_coef"]),
+        _ptr(csr["prod_ptr"]), _ptr(csr["prod_species"]), _ptr(csr["prod_coef"]),
+        _ptr(c), _ptr(x), ctypes.byref(o), _ptr(a), _ptr(crit), _ptr(sc))
+    if rc != 0:
+        raise ValueError("invalid model")
+    return {"a": a, "crit": crit.astype(bool), "a0": sc[0], "a0c": sc[1], "tau1": sc[2]}
+
+
+def default_opts(mode=MODE_TAU_LEAP, eps=0.03, n_c=10, ssa_factor=10.0, ssa_block=100,
+                 max_halvings=64, max_attempts=100_000_000) -> Opts:
+    return Opts(mode, n_c, eps, ssa_factor, ssa_block, max_halvings, max_attempts)
+
+
+def simulate(network, params, x0, t_end, sample_times, seed=0, opts=None, sim_ids=None,
+             sim_offset=0, threads=0):
+    """Run simulations of ``network`` on the CPU.
+
+    params [R, M] float64, x0 [R, N] int32, sample_times [S] float64.
+    Row r uses the random stream of simulation ``sim_ids[r]`` (or
+    ``sim_offset + r``).  Returns (samples [R, S, N] int32, stats [R]).
+    """
+    csr = network.csr()
+    N, M = network.n_species, network.n_reactions
+    params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, M)
+    R = params.shape[0]
+    x0 = np.ascontiguousarray(x0, dtype=np.int32).reshape(R, N)
+    T = np.ascontiguousarray(sample_times, dtype=np.float64)
+    S = int(T.shape[0])
+    ids = None if sim_ids is None else np.ascontiguousarray(sim_ids, dtype=np.int64)
+    samples = np.zeros((R, S, N), dtype=np.int32)
+    stats = np.zeros(R, dtype=STATS_DTYPE)
+    o = opts if opts is not None else default_opts()
+    rc = lib().oracle_simulate(
+        N, M, _ptr(csr["react_ptr"]), _ptr(csr["react_species"]), _ptr(csr["react_coef"]),
+        _ptr(csr["prod_ptr"]), _ptr(csr["prod_species"]), _ptr(csr["prod_coef"]),
+        R, _ptr(ids), int(sim_offset), _ptr(params), _ptr(x0), float(t_end), _ptr(T), S,
+        int(seed), ctypes.byref(o), _ptr(samples), _ptr(stats), int(threads))
+    if rc != 0:
+        raise ValueError("oracle rejected the model (order > 2 or bad species index)")
+    return samples, stats
+
+
+def simulate_batch(batch, seed=0, opts=None, threads=0, rows=None):
+    """Convenience wrapper over an ``inputs.Batch`` (optionally a subset of rows)."""
+    if rows is None:
+        return simulate(batch.network, batch.params, batch.x0, batch.t_end, batch.sample_times,
+                        seed, opts, threads=threads)
+    rows = np.asarray(rows, dtype=np.int64)
+    return simulate(batch.network, batch.params[rows], batch.x0[rows], batch.t_end,
+                    batch.sample_times, seed, opts, sim_ids=rows, threads=threads)
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+__all__ = ["simulate", "simulate_batch", "philox", "log_array", "exp_array", "lnfact_array",
+           "poisson_array", "canon_sum", "canon_select", "leap_quantities", "u01", "log", "exp", "lnfact", "poisson",
+           "default_opts", "Opts", "STATS_DTYPE", "MODE_TAU_LEAP", "MODE_EXACT_SSA",
+           "STATUS_NAMES", "num_threads"]
+
+_ = os  # keep import for path helpers used by build

@@ -1,0 +1,176 @@
+"""Pins for the oracle's building blocks: Philox4x32-10, the (0,1) uniform,
+the self-contained log / exp / log k!, and the canonical sum and selection.
+
+Each check compares against something other than the oracle itself:
+published known-answer values, the platform libm (within a stated ulp
+bound), exact rational arithmetic, or brute-force frequencies.
+"""
+import math
+import os
+from decimal import Decimal, getcontext
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def ulp_distance(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    ia = a.view(np.int64).astype(np.int64)
+    ib = b.view(np.int64).astype(np.int64)
+    # map to a monotone integer line (both signs)
+    ia = np.where(ia < 0, np.int64(-(2**63)) - ia, ia)
+    ib = np.where(ib < 0, np.int64(-(2**63)) - ib, ib)
+    return np.abs(ia - ib)
+
+
+# ------------------------------------------------------------------ Philox
+
+def test_philox_known_answers(oracle_lib):
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(v, 16) for v in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        assert oracle_lib.philox(r[0:4], r[4:6]) == r[6:10]
+
+
+def test_philox_counter_words_all_matter(oracle_lib):
+    base = oracle_lib.philox([1, 2, 3, 4], [5, 6])
+    for pos in range(4):
+        ctr = [1, 2, 3, 4]
+        ctr[pos] ^= 1
+        assert oracle_lib.philox(ctr, [5, 6]) != base
+    for pos in range(2):
+        key = [5, 6]
+        key[pos] ^= 1
+        assert oracle_lib.philox([1, 2, 3, 4], key) != base
+
+
+def test_u01_edges_and_exactness(oracle_lib):
+    assert oracle_lib.u01(0, 0) == 2.0 ** -53
+    assert oracle_lib.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    rng = np.random.default_rng(1)
+    for w0, w1 in rng.integers(0, 2**32, size=(200, 2)):
+        u = oracle_lib.u01(int(w0), int(w1))
+        m = ((int(w0) << 32) | int(w1)) >> 12
+        assert Fraction(u) == Fraction(2 * m + 1, 2**53)
+        assert 0.0 < u < 1.0
+
+
+# ------------------------------------------------------- log / exp / log k!
+
+def test_log_within_2ulp_of_libm(oracle_lib):
+    rng = np.random.default_rng(2)
+    x = np.concatenate([
+        rng.uniform(0.0, 1.0, 100_000),
+        np.exp(rng.uniform(-700, 700, 100_000)),
+        1.0 + rng.uniform(-1e-6, 1e-6, 20_000),
+        np.array([2.0 ** -53, 1 - 2.0 ** -53, 0.5, 1.0, 2.0, math.sqrt(2.0), math.sqrt(0.5),
+                  5e-324, 2.2250738585072014e-308, 1e-310, 1.7976931348623157e308]),
+    ])
+    x = x[x > 0]
+    y = oracle_lib.log_array(x)
+    ref = np.log(x)
+    d = ulp_distance(y, ref)
+    assert d.max() <= 2, (x[d.argmax()], y[d.argmax()], ref[d.argmax()])
+    assert oracle_lib.log(1.0) == 0.0
+
+
+def test_log_against_high_precision(oracle_lib):
+    getcontext().prec = 50
+    rng = np.random.default_rng(3)
+    for x in np.concatenate([rng.uniform(1e-9, 1.0, 300), rng.uniform(1.0, 1e9, 300)]):
+        exact = Decimal(float(x)).ln()
+        got = Decimal(oracle_lib.log(float(x)))
+        ulp = Decimal(math.ulp(float(exact)))
+        assert abs(got - exact) <= 2 * ulp
+
+
+def test_exp_within_2ulp_of_libm(oracle_lib):
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.uniform(-10.0, 0.0, 100_000), rng.uniform(-700, 700, 100_000),
+                        rng.uniform(-1e-8, 1e-8, 10_000), np.array([0.0, -1.0, 1.0, -10.0])])
+    y = oracle_lib.exp_array(x)
+    d = ulp_distance(y, np.exp(x))
+    assert d.max() <= 2, x[d.argmax()]
+    assert oracle_lib.exp(0.0) == 1.0
+
+
+def test_lnfact_exact_small_and_stirling_large(oracle_lib):
+    getcontext().prec = 60
+    ks = np.array(list(range(0, 200)) + [500, 1000, 4096], dtype=np.int64)
+    got = oracle_lib.lnfact_array(ks)
+    for k, g in zip(ks, got):
+        exact = Decimal(math.factorial(int(k))).ln() if k > 1 else Decimal(0)
+        tol = 4 * Decimal(math.ulp(float(exact))) if k > 1 else Decimal(0)
+        assert abs(Decimal(g) - exact) <= tol, (k, g, exact)
+    big = np.array([10**5, 10**6, 10**9, 2**40], dtype=np.int64)
+    gb = oracle_lib.lnfact_array(big)
+    for k, g in zip(big, gb):
+        ref = math.lgamma(float(k) + 1.0)
+        assert abs(g - ref) <= 1e-14 * ref
+
+
+# ---------------------------------------------- canonical sum and selection
+
+def test_canon_sum_matches_exact_sum(oracle_lib):
+    rng = np.random.default_rng(5)
+    for M in (1, 3, 31, 32, 33, 64, 100, 512):
+        v = rng.uniform(0, 1, M) * 10.0 ** rng.integers(-3, 4, M)
+        exact = math.fsum(v)
+        assert abs(oracle_lib.canon_sum(v) - exact) <= 8 * math.ulp(exact)
+
+
+def test_canon_sum_order_is_the_slot_tree(oracle_lib):
+    # the slot tree adds v[l] and v[l+16] first: with v[0]=1, v[16]=-1 and
+    # v[1]=1e-16 (cancelled to 0 by a left-to-right sum) the tree keeps it.
+    v = np.zeros(32)
+    v[0], v[16], v[1] = 1.0, -1.0, 1e-16
+    assert oracle_lib.canon_sum(v) == 1e-16
+    assert ((1.0 + 1e-16) - 1.0) == 0.0
+
+
+def test_canon_select_frequencies_and_zero_weights(oracle_lib):
+    rng = np.random.default_rng(6)
+    for M in (1, 2, 5, 32, 64, 77):
+        v = rng.uniform(0, 1, M)
+        v[rng.random(M) < 0.3] = 0.0
+        if v.sum() == 0:
+            v[-1] = 0.5
+        K = 20_000
+        counts = np.zeros(M)
+        for i in range(K):
+            counts[oracle_lib.canon_select(v, (i + 0.5) / K)] += 1
+        assert np.all(counts[v == 0.0] == 0)
+        # a deterministic grid of u gives each j its share up to the boundaries
+        np.testing.assert_allclose(counts / K, v / v.sum(), atol=2.0 / K)
+
+
+def test_canon_select_extremes(oracle_lib):
+    # the descent decides the slot index from its lowest bit upwards, so
+    # slots are visited in bit-reversed order: slot 4 (00100 -> 00100)
+    # precedes slot 2 (00010 -> 01000).
+    v = np.array([0.0, 0.0, 3.0, 0.0, 1.0, 0.0])
+    assert oracle_lib.canon_select(v, 2.0 ** -53) == 4
+    assert oracle_lib.canon_select(v, 1 - 2.0 ** -53) == 2
+    assert oracle_lib.canon_select(v, 0.24) == 4
+    assert oracle_lib.canon_select(v, 0.26) == 2
+    # inside one slot the walk is in increasing j: v[3] and v[35] share slot 3
+    w = np.zeros(40)
+    w[3], w[35] = 1.0, 1.0
+    assert oracle_lib.canon_select(w, 0.49) == 3
+    assert oracle_lib.canon_select(w, 0.51) == 35
+
+
+@pytest.mark.parametrize("u", [0.0, 0.999999999])
+def test_canon_select_single_positive(oracle_lib, u):
+    v = np.zeros(70)
+    v[45] = 2.5
+    assert oracle_lib.canon_select(v, u) == 45
