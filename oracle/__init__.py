@@ -22,7 +22,7 @@ from . import build as _build
 
 MODE_TAU_LEAP = 0
 MODE_EXACT_SSA = 1
-STATUS_NAMES = {0: "OK", 1: "STEP_LIMIT", 2: "OVERFLOW", 3: "REJECT_LIMIT"}
+STATUS_NAMES = {0: "OK", 1: "STEP_LIMIT", 2: "OVERFLOW", 3: "REJECT_LIMIT", 4: "INVALID"}
 
 
 class Opts(ctypes.Structure):

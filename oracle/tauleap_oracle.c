@@ -36,6 +36,7 @@
  * Pinning: see tests/test_oracle_*.py (closed forms, exact CME solutions,
  * libm ulp bounds, Poisson pmf, Philox known-answer values, invariants).
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -47,7 +48,7 @@
 /* ------------------------------------------------------------------ */
 /* status codes and options                                            */
 /* ------------------------------------------------------------------ */
-enum { ST_OK = 0, ST_STEP_LIMIT = 1, ST_OVERFLOW = 2, ST_REJECT_LIMIT = 3 };
+enum { ST_OK = 0, ST_STEP_LIMIT = 1, ST_OVERFLOW = 2, ST_REJECT_LIMIT = 3, ST_INVALID = 4 };
 enum { MODE_TAU_LEAP = 0, MODE_EXACT_SSA = 1 };
 enum { PURPOSE_LEAP = 1, PURPOSE_POISSON = 2, PURPOSE_SSA = 3 };
 
@@ -242,6 +243,7 @@ int64_t oracle_poisson(double lam, uint64_t seed, uint32_t sim, uint32_t attempt
 {
     uint32_t w[4];
     if (!(lam > 0.0)) return 0;
+    if (!(lam < 0x1p40)) return COUNT_LIMIT + 1;   /* mean beyond the count limit */
     if (lam < 10.0) {
         /* inversion by sequential search: smallest k with u <= F(k) */
         draw_block(seed, sim, attempt, PURPOSE_POISSON, j, 0, w);
@@ -546,6 +548,7 @@ static void simulate_one(const model_t *m, const oracle_opts *o, uint64_t seed, 
         for (int j = 0; j < M; ++j) w->a[j] = propensity(m, j, c[j], x);
         double a0 = canon_sum(w->a, M, levels);
         if (a0 == 0.0) { t = t_end; break; }   /* no reaction can fire again */
+        if (!(a0 <= DBL_MAX)) { st->status = ST_INVALID; break; }   /* non-finite rates */
 
         int do_ssa = (o->mode == MODE_EXACT_SSA);
         double tau1 = INFINITY, a0c = 0.0;
@@ -565,6 +568,7 @@ static void simulate_one(const model_t *m, const oracle_opts *o, uint64_t seed, 
                         a0 = canon_sum(w->a, M, levels);
                     }
                     if (a0 == 0.0) { t = t_end; goto finished; }
+                    if (!(a0 <= DBL_MAX)) { st->status = ST_INVALID; goto finished; }
                     if ((int64_t)attempt >= o->max_attempts) { st->status = ST_STEP_LIMIT; goto finished; }
                     attempt = attempt + 1;
                     uint32_t wb[4];
@@ -577,6 +581,7 @@ static void simulate_one(const model_t *m, const oracle_opts *o, uint64_t seed, 
                     record_until(out, N, x, T, S, &ks, t_new, 1);
                     if (t_new > t_end) { t = t_end; goto finished; }
                     int jf = canon_select(w->a, M, levels, u2 * a0);
+                    if (jf < 0) { st->status = ST_INVALID; goto finished; }
                     int overflow = 0;
                     for (int e = m->nu_ptr[jf]; e < m->nu_ptr[jf + 1]; ++e) {
                         int64_t nx = (int64_t)x[m->nu_sp[e]] + m->nu_val[e];
