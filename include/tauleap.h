@@ -1,0 +1,182 @@
+/*
+ * tauleap.h -- C ABI of the B300 batched stochastic-simulation engine.
+ *
+ * The engine runs many independent stochastic simulations of one
+ * mass-action reaction network at once, each with its own kinetic constants
+ * and initial molecule counts.  This is the parameter-sweep workload of the
+ * paper's "Aims and motivation" section, where all simulations of a sweep are
+ * mutually independent (Methods, last paragraph).  One CUDA thread group
+ * advances one simulation.
+ *
+ * Method, per simulation (Methods section: X(t) is a continuous-time Markov
+ * chain over molecule counts, sampled by Gillespie's algorithm):
+ *   - tau-leaping with the step-size selection of Cao, Gillespie & Petzold
+ *     (J. Chem. Phys. 124, 044109, 2006) and the critical-reaction rule of
+ *     Cao, Gillespie & Petzold (J. Chem. Phys. 123, 054104, 2005),
+ *   - falling back to blocks of exact SSA steps (direct method) when the
+ *     admissible leap is shorter than a few mean reaction times,
+ *   - or exact SSA only (SSA_MODE_EXACT).
+ * Random numbers come from Philox4x32-10 counter-based streams.  A
+ * simulation's stream is keyed by (seed, global simulation index), so results
+ * do not depend on batch composition, launch shape or sharding.
+ *
+ * Conventions
+ *   - Every entry point returns SSA_OK (0) or a negative SSA_E* code.
+ *     ssa_last_error() then holds a message for the calling thread.
+ *   - Per-simulation failures (step cap, count overflow) are not call
+ *     errors: they are reported in ssa_sim_stats.status.  The samples after
+ *     a failure repeat the last valid state.
+ *   - Index arrays are int32 and rates / times are IEEE double.  All
+ *     arrays are dense, row-major and C-contiguous.
+ *   - Handles are not shared between threads without external locking.
+ *     Different handles may be used concurrently.
+ *   - Any CUDA failure is reported as SSA_ECUDA with the CUDA error string.
+ */
+#ifndef TAULEAP_H
+#define TAULEAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSA_ABI_VERSION 1
+
+/* return codes */
+#define SSA_OK 0
+#define SSA_EINVAL (-1)       /* bad argument or model */
+#define SSA_ENOMEM (-2)       /* the job's HBM footprint does not fit */
+#define SSA_EBUSY (-3)        /* job still running (ssa_poll-based callers) */
+#define SSA_ECUDA (-4)        /* CUDA runtime error */
+#define SSA_EUNSUPPORTED (-5) /* option combination not built */
+
+/* per-simulation status (ssa_sim_stats.status) */
+#define SSA_STATUS_OK 0
+#define SSA_STATUS_STEP_LIMIT 1   /* max_attempts leap attempts + SSA steps used */
+#define SSA_STATUS_OVERFLOW 2     /* a count passed 2^31-1 or a leap drew > 2^40 */
+#define SSA_STATUS_REJECT_LIMIT 3 /* max_halvings negativity retries in one leap */
+#define SSA_STATUS_INVALID 4      /* the propensity sum a0 was not finite (bad rates) */
+
+/* job states (ssa_poll) */
+#define SSA_JOB_RUNNING 1
+#define SSA_JOB_DONE 2
+#define SSA_JOB_FAILED 3
+
+/* ssa_options.mode */
+#define SSA_MODE_TAU_LEAP 0 /* CGP tau-leaping with critical reactions + SSA fallback */
+#define SSA_MODE_EXACT 1    /* Gillespie direct method only */
+
+/* ssa_options.precision */
+#define SSA_FP64_REF 0 /* bit-identical to the FP64 reference algorithm */
+
+/* ssa_options.layout */
+#define SSA_LAYOUT_AUTO 0
+#define SSA_LAYOUT_WARP 1 /* one warp (32 lanes) per simulation */
+
+typedef struct ssa_model *ssa_model_t;
+typedef struct ssa_job *ssa_job_t;
+
+/*
+ * A reaction network (Methods: reactions fire between species and change
+ * the state vector X of molecule counts).  This is reaction-major CSR.
+ * Reaction j consumes react_coef[e] molecules of species react_species[e]
+ * for e in [react_ptr[j], react_ptr[j+1]), and produces products in the same
+ * way.  The reaction order (sum of reactant coefficients) must be <= 2.
+ * Coefficients are >= 1, and product coefficients are <= 100.  A species
+ * appears at most once per row.  Arrays are caller-owned and are read only
+ * during ssa_load_model.
+ */
+typedef struct {
+    int32_t n_species;   /* N, 1..16384 */
+    int32_t n_reactions; /* M, 1..16384 */
+    const int32_t *react_ptr, *react_species, *react_coef;
+    const int32_t *prod_ptr, *prod_species, *prod_coef;
+} ssa_model_desc;
+
+typedef struct {
+    int32_t mode;         /* SSA_MODE_* (default TAU_LEAP) */
+    int32_t precision;    /* SSA_FP64_REF */
+    double eps;           /* CGP error-control parameter epsilon (0.03) */
+    int32_t n_c;          /* critical threshold: L_j < n_c (10) */
+    int32_t ssa_block;    /* SSA steps per fallback block (100) */
+    double ssa_factor;    /* fall back when tau' < ssa_factor / a0 (10) */
+    int32_t max_halvings; /* negativity retries per leap (64) */
+    int32_t layout;       /* SSA_LAYOUT_* (AUTO) */
+    int64_t max_attempts; /* per-simulation cap on leap attempts + SSA steps (1e8) */
+    int32_t block_warps;  /* warps per CTA, 0 = automatic */
+    int32_t reserved;
+} ssa_options;
+
+/* Per-simulation counters and status (56 bytes). */
+typedef struct {
+    int32_t status;    /* SSA_STATUS_* */
+    int32_t reserved;
+    int64_t leaps;     /* accepted tau-leaps */
+    int64_t rejected;  /* leap attempts undone because a count went negative */
+    int64_t ssa_steps; /* reactions fired by exact SSA steps */
+    int64_t firings;   /* total reaction firings (leap Poisson counts + SSA events) */
+    int64_t attempts;  /* random-stream attempt counter at exit */
+    double t_final;    /* simulated time reached */
+} ssa_sim_stats;
+
+/* Fill *opts with the defaults listed above. */
+void ssa_default_options(ssa_options *opts);
+
+/* Validate a network and upload it to the current CUDA device.  On success
+ * *out is a handle that owns the device copy; free it with ssa_free_model.
+ * Fails with SSA_EINVAL for order > 2, a species index out of range, a
+ * coefficient out of range, or a repeated species in one row. */
+int ssa_load_model(const ssa_model_desc *desc, ssa_model_t *out);
+int ssa_free_model(ssa_model_t model);
+int ssa_model_info(ssa_model_t model, int32_t *n_species, int32_t *n_reactions);
+
+/* Enqueue n_sims simulations on `stream` (a cudaStream_t, NULL = legacy
+ * default stream).  All array arguments are DEVICE pointers on the model's
+ * device, caller-owned, and must stay valid until the stream reaches this
+ * work:
+ *   params       [n_sims][M] double  stochastic rate constants c_j (>= 0)
+ *   x0           [n_sims][N] int32   initial counts (>= 0)
+ *   sample_times [n_samples] double  non-decreasing, within [0, t_end]
+ *   samples      [n_sims][n_samples][N] int32 output: X at each sample time
+ *   stats        [n_sims] ssa_sim_stats output (may be NULL)
+ * Simulation r uses the random stream of global index sim_offset + r
+ * (sim_offset + n_sims <= 2^32).  Returns as soon as the launch is queued;
+ * the function allocates a small stream-ordered work counter and frees it
+ * on the same stream. */
+int ssa_simulate_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
+                     const double *params, const int32_t *x0, double t_end,
+                     const double *sample_times, int32_t n_samples, uint64_t seed,
+                     const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
+                     void *stream);
+
+/* Host-buffer form.  Copies the HOST inputs to device memory that the job
+ * owns and enqueues the simulation on `stream` (NULL = a stream the job
+ * creates).  The inputs may be reused once this returns.  Fails with
+ * SSA_ENOMEM if the job's device footprint exceeds the free HBM.  Complete the
+ * job with ssa_poll / ssa_wait and ssa_fetch, then free it with
+ * ssa_release_job. */
+int ssa_submit_batch(ssa_model_t model, int64_t n_sims, const double *params,
+                     const int32_t *x0, double t_end, const double *sample_times,
+                     int32_t n_samples, uint64_t seed, const ssa_options *opts,
+                     void *stream, ssa_job_t *out);
+
+/* Non-blocking: *state = SSA_JOB_RUNNING, SSA_JOB_DONE or SSA_JOB_FAILED. */
+int ssa_poll(ssa_job_t job, int32_t *state);
+/* Block until the job's work is complete. */
+int ssa_wait(ssa_job_t job);
+/* Wait for the job, then copy its results to HOST buffers:
+ * samples [n_sims][n_samples][N] int32, stats [n_sims] (either may be NULL). */
+int ssa_fetch(ssa_job_t job, int32_t *samples, ssa_sim_stats *stats);
+/* Wait for the job and free everything it owns. */
+int ssa_release_job(ssa_job_t job);
+
+/* Message describing the last failed call on this thread ("" if none). */
+const char *ssa_last_error(void);
+int ssa_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TAULEAP_H */

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of ``libtauleap.so`` (C ABI in ``include/tauleap.h``).
+
+Argument marshalling only: every step of the simulation runs inside the
+CUDA library.  Device arrays are passed as torch CUDA tensors (their
+``data_ptr()``), host arrays as numpy arrays.  The library must have been
+built (``paper_1309_7695_b300.build``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtauleap.so")
+
+SSA_OK = 0
+SSA_EINVAL = -1
+SSA_ENOMEM = -2
+SSA_EBUSY = -3
+SSA_ECUDA = -4
+SSA_EUNSUPPORTED = -5
+
+SSA_STATUS_OK = 0
+SSA_STATUS_STEP_LIMIT = 1
+SSA_STATUS_OVERFLOW = 2
+SSA_STATUS_REJECT_LIMIT = 3
+SSA_STATUS_INVALID = 4
+
+SSA_JOB_RUNNING = 1
+SSA_JOB_DONE = 2
+SSA_JOB_FAILED = 3
+
+SSA_MODE_TAU_LEAP = 0
+SSA_MODE_EXACT = 1
+SSA_FP64_REF = 0
+SSA_LAYOUT_AUTO = 0
+SSA_LAYOUT_WARP = 1
+
+EXPORTED = [
+    "ssa_default_options", "ssa_load_model", "ssa_free_model", "ssa_model_info",
+    "ssa_simulate_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
+    "ssa_release_job", "ssa_last_error", "ssa_abi_version",
+]
+
+
+class SsaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_species", ctypes.c_int32), ("n_reactions", ctypes.c_int32),
+        ("react_ptr", ctypes.c_void_p), ("react_species", ctypes.c_void_p), ("react_coef", ctypes.c_void_p),
+        ("prod_ptr", ctypes.c_void_p), ("prod_species", ctypes.c_void_p), ("prod_coef", ctypes.c_void_p),
+    ]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("eps", ctypes.c_double),
+        ("n_c", ctypes.c_int32), ("ssa_block", ctypes.c_int32), ("ssa_factor", ctypes.c_double),
+        ("max_halvings", ctypes.c_int32), ("layout", ctypes.c_int32), ("max_attempts", ctypes.c_int64),
+        ("block_warps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+STATS_DTYPE = np.dtype([
+    ("status", np.int32), ("reserved", np.int32), ("leaps", np.int64), ("rejected", np.int64),
+    ("ssa_steps", np.int64), ("firings", np.int64), ("attempts", np.int64), ("t_final", np.float64),
+])
+assert STATS_DTYPE.itemsize == 56
+
+_lib = None
+
+
+def lib():
+    """Load libtauleap.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1309_7695_b300.build` "
+                          "(or __graft_entry__.build()) first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    L.ssa_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.ssa_default_options.restype = None
+    L.ssa_load_model.argtypes = [ctypes.POINTER(ModelDesc), ctypes.POINTER(vp)]
+    L.ssa_free_model.argtypes = [vp]
+    L.ssa_model_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.ssa_simulate_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp, vp, vp]
+    L.ssa_submit_batch.argtypes = [vp, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp,
+                                   ctypes.POINTER(vp)]
+    L.ssa_poll.argtypes = [vp, ctypes.POINTER(i32)]
+    L.ssa_wait.argtypes = [vp]
+    L.ssa_fetch.argtypes = [vp, vp, vp]
+    L.ssa_release_job.argtypes = [vp]
+    L.ssa_last_error.argtypes = []
+    L.ssa_last_error.restype = ctypes.c_char_p
+    L.ssa_abi_version.argtypes = []
+    for name in EXPORTED:
+        if name not in ("ssa_default_options", "ssa_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != SSA_OK:
+        raise SsaError(rc, lib().ssa_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def ssa_default_options(**overrides) -> Options:
+    o = Options()
+    lib().ssa_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class Model:
+    """A network loaded on the current CUDA device (ssa_load_model)."""
+
+    def __init__(self, network):
+        csr = network.csr()
+        self._keep = csr
+        d = ModelDesc(network.n_species, network.n_reactions,
+                      _ptr(csr["react_ptr"]), _ptr(csr["react_species"]), _ptr(csr["react_coef"]),
+                      _ptr(csr["prod_ptr"]), _ptr(csr["prod_species"]), _ptr(csr["prod_coef"]))
+        h = ctypes.c_void_p()
+        _check(lib().ssa_load_model(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.n_species = network.n_species
+        self.n_reactions = network.n_reactions
+
+    def close(self):
+        if self.handle:
+            lib().ssa_free_model(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ssa_load_model(network) -> Model:
+    return Model(network)
+
+
+def ssa_simulate_dev(model: Model, params, x0, t_end, sample_times, samples, stats=None, seed=0,
+                     opts=None, sim_offset=0, stream=None):
+    """Enqueue simulations on device tensors (torch CUDA tensors).
+
+    params [n, M] float64, x0 [n, N] int32, sample_times [S] float64,
+    samples [n, S, N] int32 (output), stats [n * 56] uint8 or None (output).
+    ``stream``: a torch.cuda.Stream or raw handle (default: torch's current).
+    """
+    n = int(params.shape[0]) if params.dim() == 2 else 0
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    o = opts if opts is not None else ssa_default_options()
+    _check(lib().ssa_simulate_dev(model.handle, n, int(sim_offset), _ptr(params), _ptr(x0), float(t_end),
+                                  _ptr(sample_times), int(sample_times.numel()), int(seed), ctypes.byref(o),
+                                  _ptr(samples), _ptr(stats), ctypes.c_void_p(int(handle))))
+
+
+class Job:
+    """A host-buffer job (ssa_submit_batch / ssa_poll / ssa_fetch / ssa_release_job)."""
+
+    def __init__(self, model: Model, handle, n_sims, n_samples):
+        self.model, self.handle, self.n_sims, self.n_samples = model, handle, n_sims, n_samples
+
+    def poll(self) -> int:
+        st = ctypes.c_int32()
+        _check(lib().ssa_poll(self.handle, ctypes.byref(st)))
+        return st.value
+
+    def wait(self):
+        _check(lib().ssa_wait(self.handle))
+
+    def fetch(self, samples=None, stats=None):
+        if samples is None:
+            samples = np.empty((self.n_sims, self.n_samples, self.model.n_species), dtype=np.int32)
+        if stats is None:
+            stats = np.empty(self.n_sims, dtype=STATS_DTYPE)
+        _check(lib().ssa_fetch(self.handle, _ptr(samples), _ptr(stats)))
+        return samples, stats
+
+    def release(self):
+        if self.handle:
+            _check(lib().ssa_release_job(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def ssa_submit_batch(model: Model, params, x0, t_end, sample_times, seed=0, opts=None, stream=None) -> Job:
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x0 = np.ascontiguousarray(x0, dtype=np.int32)
+    T = np.ascontiguousarray(sample_times, dtype=np.float64)
+    n = int(params.shape[0])
+    o = opts if opts is not None else ssa_default_options()
+    h = ctypes.c_void_p()
+    s = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(lib().ssa_submit_batch(model.handle, n, _ptr(params), _ptr(x0), float(t_end), _ptr(T), int(T.size),
+                                  int(seed), ctypes.byref(o), s, ctypes.byref(h)))
+    return Job(model, h, n, int(T.size))
+
+
+def simulate_host(network, params, x0, t_end, sample_times, seed=0, opts=None):
+    """Convenience: load, submit, fetch and release; returns (samples, stats)."""
+    m = Model(network)
+    try:
+        j = ssa_submit_batch(m, params, x0, t_end, sample_times, seed, opts)
+        try:
+            return j.fetch()
+        finally:
+            j.release()
+    finally:
+        m.close()

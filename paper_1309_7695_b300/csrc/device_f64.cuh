@@ -1,0 +1,215 @@
+// Device arithmetic of the FP64 reference mode.
+//
+// Every function here is a fixed sequence of correctly rounded IEEE-754
+// double operations (add, sub, mul, div, sqrt) plus exact bit manipulation,
+// compiled with -fmad=false so no multiply-add is fused.  A CPU program that
+// performs the same operations in the same order gets bit-identical values.
+// No CUDA math-library transcendental is used.
+#pragma once
+
+#include <stdint.h>
+
+#include "engine.h"
+
+namespace tl {
+namespace f64 {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds; each round
+// multiplies counter words 0 and 2 by the two round constants, mixes the
+// high halves with words 1 and 3 and the key, and the key advances by the
+// two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Stream block (sim, attempt, purpose<<24 | j, block) under key = seed.
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t purpose,
+                                      uint32_t j, uint32_t block)
+{
+    return philox4x32_10(make_uint4(sim, attempt, (purpose << 24) | j, block), (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+}
+
+// Uniform in (0,1): with m the top 52 bits of (w0:w1), the value
+// (2m + 1) * 2^-53.  It is exact in double, so it is assembled from integer
+// bits here: the odd 53-bit integer 2m+1 is normalised with a leading-zero
+// count and given the matching exponent.
+__device__ __forceinline__ double u01(uint32_t w0, uint32_t w1)
+{
+    const uint64_t m = ((((uint64_t)w0) << 32) | (uint64_t)w1) >> 12;
+    const uint64_t n = 2 * m + 1;                   // odd, < 2^53
+    const int lz = __clzll((long long)n);           // >= 11
+    const uint64_t mant = (n << (lz - 11)) & 0x000FFFFFFFFFFFFFull;
+    const uint64_t expo = (uint64_t)(1033 - lz);    // value = n * 2^-53
+    return __longlong_as_double((long long)((expo << 52) | mant));
+}
+
+// ------------------------------------------------------ log, exp, log k!
+// ln 2 split: the high part keeps 32 significant bits so that e * LN2_HI
+// is exact for every exponent e that occurs.
+#define TL_LN2_HI 0x1.62e42feep-1
+#define TL_LN2_LO 0x1.a39ef35793c76p-33
+#define TL_INV_LN2 0x1.71547652b82fep+0
+#define TL_SQRT2 0x1.6a09e667f3bcdp+0
+#define TL_HALF_LN_2PI 0x1.d67f1c864beb5p-1
+
+// ln x for finite x > 0: x = 2^e m, m in [sqrt2/2, sqrt2]; ln m = 2 atanh(s)
+// with s = (m-1)/(m+1) and atanh(s)/s = sum_n s^(2n)/(2n+1), kept through
+// the s^20 term, evaluated in Horner form in z = s^2.
+__device__ __forceinline__ double dlog(double x)
+{
+    long long bits = __double_as_longlong(x);
+    int biased = (int)((bits >> 52) & 0x7ff);
+    int adj = 0;
+    if (biased == 0) {
+        x = x * 0x1p54;
+        bits = __double_as_longlong(x);
+        biased = (int)((bits >> 52) & 0x7ff);
+        adj = -54;
+    }
+    int e = biased - 1023 + adj;
+    double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    if (m > TL_SQRT2) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double z = s * s;
+    double p = 1.0 / 21.0;
+    p = p * z + 1.0 / 19.0;
+    p = p * z + 1.0 / 17.0;
+    p = p * z + 1.0 / 15.0;
+    p = p * z + 1.0 / 13.0;
+    p = p * z + 1.0 / 11.0;
+    p = p * z + 1.0 / 9.0;
+    p = p * z + 1.0 / 7.0;
+    p = p * z + 1.0 / 5.0;
+    p = p * z + 1.0 / 3.0;
+    const double two_s = 2.0 * s;
+    const double lm = two_s + two_s * (z * p);
+    const double de = (double)e;
+    return de * TL_LN2_HI + (lm + de * TL_LN2_LO);
+}
+
+// e^x: n = floor(x/ln2 + 1/2), r = (x - n LN2_HI) - n LN2_LO, e^r by the
+// Taylor polynomial through r^13 in Horner form, then scaled by 2^n.
+__device__ __forceinline__ double dexp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.0) return __longlong_as_double(0x7FF0000000000000ll);
+    if (x < -745.0) return 0.0;
+    const double n = floor(x * TL_INV_LN2 + 0.5);
+    const double r = (x - n * TL_LN2_HI) - n * TL_LN2_LO;
+    double p = 1.0 / 6227020800.0;
+    p = p * r + 1.0 / 479001600.0;
+    p = p * r + 1.0 / 39916800.0;
+    p = p * r + 1.0 / 3628800.0;
+    p = p * r + 1.0 / 362880.0;
+    p = p * r + 1.0 / 40320.0;
+    p = p * r + 1.0 / 5040.0;
+    p = p * r + 1.0 / 720.0;
+    p = p * r + 1.0 / 120.0;
+    p = p * r + 1.0 / 24.0;
+    p = p * r + 1.0 / 6.0;
+    p = p * r + 1.0 / 2.0;
+    p = p * r + 1.0;
+    p = p * r + 1.0;
+    int ni = (int)n;
+    if (ni < -1020) {
+        p = p * 0x1p-60;
+        ni += 60;
+    }
+    return p * __longlong_as_double((long long)((uint64_t)(ni + 1023) << 52));
+}
+
+// ln k!: exact product then ln for k < 10; Stirling's series through the
+// k^-13 term for k >= 10.
+__device__ __forceinline__ double dlnfact(long long k)
+{
+    if (k < 10) {
+        double f = 1.0;
+        for (long long i = 2; i <= k; ++i) f = f * (double)i;
+        return dlog(f);
+    }
+    const double kd = (double)k;
+    const double r = 1.0 / kd;
+    const double r2 = r * r;
+    double ser = 1.0 / 156.0;
+    ser = ser * r2 - 691.0 / 360360.0;
+    ser = ser * r2 + 1.0 / 1188.0;
+    ser = ser * r2 - 1.0 / 1680.0;
+    ser = ser * r2 + 1.0 / 1260.0;
+    ser = ser * r2 - 1.0 / 360.0;
+    ser = ser * r2 + 1.0 / 12.0;
+    ser = ser * r;
+    return ((kd + 0.5) * dlog(kd) - kd) + (TL_HALF_LN_2PI + ser);
+}
+
+// --------------------------------------------------------------- Poisson
+constexpr long long kCountLimit = 1ll << 40;
+constexpr int kInversionCap = 100;
+constexpr int kPtrsMaxIters = 1000;
+
+// k ~ Poisson(lam) on the stream (sim, attempt, reaction j).  Means below 10:
+// inversion by sequential search with one uniform (stop early once a term no
+// longer changes the running cdf).  Means >= 10: PTRS, transformed rejection
+// with squeeze (Hormann 1993), one stream block per iteration.  Returns -1
+// if PTRS exhausts its iteration cap and kCountLimit + 1 for a draw above
+// kCountLimit.  `inv` holds 1/k for k = 1..kInversionCap (correctly rounded,
+// so identical to dividing).
+__device__ __forceinline__ long long poisson(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                             uint32_t j, const double *__restrict__ inv)
+{
+    if (!(lam > 0.0)) return 0;
+    if (!(lam < 0x1p40)) return kCountLimit + 1;
+    if (lam < 10.0) {
+        const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, 0);
+        const double u = u01(w.x, w.y);
+        double p = dexp(-lam);
+        double F = p;
+        long long k = 0;
+        while (u > F && k < kInversionCap) {
+            k = k + 1;
+            p = (p * lam) * inv[k];
+            const double Fn = F + p;
+            if (Fn == F) break;
+            F = Fn;
+        }
+        return k;
+    }
+    const double slam = sqrt(lam);
+    const double loglam = dlog(lam);
+    const double b = 0.931 + 2.53 * slam;
+    const double a = -0.059 + 0.02483 * b;
+    const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+    const double vr = 0.9277 - 3.6224 / (b - 2.0);
+    for (uint32_t it = 0; it < (uint32_t)kPtrsMaxIters; ++it) {
+        const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
+        const double U = u01(w.x, w.y) - 0.5;
+        const double V = u01(w.z, w.w);
+        const double us = 0.5 - fabs(U);
+        const double kd = floor((2.0 * a / us + b) * U + lam + 0.43);
+        if (us >= 0.07 && V <= vr) return (kd > (double)kCountLimit) ? kCountLimit + 1 : (long long)kd;
+        if (kd < 0.0 || (us < 0.013 && V > us)) continue;
+        if (kd > (double)kCountLimit) return kCountLimit + 1;
+        const double lhs = dlog(V * inv_alpha / (a / (us * us) + b));
+        const double rhs = -lam + kd * loglam - dlnfact((long long)kd);
+        if (lhs <= rhs) return (long long)kd;
+    }
+    return -1;
+}
+
+}  // namespace f64
+}  // namespace tl

@@ -1,0 +1,78 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tauleap.h"
+
+namespace tl {
+
+// Packed network, one int32 blob (uploaded once, staged into shared memory
+// by every CTA).  Sections, in order:
+//   rinfo [M]      kind | sp0 << 2 | sp1 << 17   (kind 0: order 0, 1: X,
+//                  2: X+Y with sp0 < sp1, 3: 2X)
+//   nu_ptr [M+1]   net-change CSR of reaction j
+//   nu_ent [nnz]   species << 8 | (nu & 0xff)    species ascending
+//   tr_ptr [N+1]   transpose: reactions that change species i
+//   tr_ent [nnz]   j << 8 | (nu & 0xff)          j ascending
+//   hor [N]        highest-order class of species i: 0 none, 1 first order,
+//                  2 second order as X+Y only, 3 some reaction takes 2X
+struct ModelLayout {
+    int32_t N, M, nnz;
+    int32_t off_rinfo, off_nu_ptr, off_nu_ent, off_tr_ptr, off_tr_ent, off_hor;
+    int32_t words;
+    int32_t max_nu_len;
+};
+
+enum : uint32_t { PURPOSE_LEAP = 1u, PURPOSE_POISSON = 2u, PURPOSE_SSA = 3u };
+
+struct SimArgs {
+    ModelLayout L;
+    const int32_t *blob;
+    const double *params;
+    const int32_t *x0;
+    const double *T;
+    int32_t S;
+    double t_end;
+    int64_t n_sims;
+    int64_t sim_offset;
+    uint64_t seed;
+    int32_t mode;
+    int32_t n_c;
+    double eps;
+    double ssa_factor;
+    int32_t ssa_block;
+    int32_t max_halvings;
+    int64_t max_attempts;
+    int32_t *samples;
+    ssa_sim_stats *stats;
+    unsigned long long *work_counter;
+};
+
+// Shared-memory bytes of one warp's simulation workspace.
+__host__ __device__ inline size_t warp_workspace_bytes(int N, int M)
+{
+    auto r16 = [](size_t v) { return (v + 15) & ~size_t(15); };
+    size_t b = 0;
+    b += r16(8 * (size_t)M);        // a_j
+    b += r16(8 * (size_t)M);        // c_j
+    b += r16(8 * (size_t)M);        // k_j
+    b += r16(8 * (size_t)N);        // x' (int64)
+    b += r16(4 * (size_t)N);        // x
+    b += r16((size_t)M);            // critical flags
+    b += r16((size_t)N);            // I_rs flags
+    return b;
+}
+
+__host__ __device__ inline size_t model_smem_bytes(const ModelLayout &L)
+{
+    return ((size_t)L.words * 4 + 15) & ~size_t(15);
+}
+
+// Warp-per-simulation FP64 reference kernel (kernel_warp_f64.cu).
+size_t warp_f64_smem_bytes(const ModelLayout &L, int block_warps);
+cudaError_t launch_warp_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+int warp_ref_occupancy(int block_warps, size_t smem);
+
+}  // namespace tl
