@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched tau-leaping engine.
+
+Workload (default): one random mass-action network of 32 species and 64
+reactions (orders 0/1/2 in ratio 1:2:1), 65,536 parameterizations with rate
+constants log-uniform in [1e-4, 1] and initial counts uniform in {0..1000},
+t_end = 100 with 101 sample times, epsilon = 0.03, n_c = 10, FP64 reference
+mode (bit-exact with the CPU oracle).  Every simulation runs to t_end or to a
+budget of 2^20 leap attempts + SSA steps.
+
+A step is one launch that simulates the whole batch (inputs resident in
+HBM).  Reported: reaction firings/s (value) and sim-steps/s (accepted leaps
++ SSA events), the same metric end to end through the host-buffer C ABI
+(e2e), the roofline position of the simulation kernel, and the CPU oracle
+on a bounded sample of the same workload (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+Multi-GPU (torchrun, one rank per GPU): each rank simulates its own 65,536
+simulations (global indices rank*65536 + r), so per-GPU work is fixed
+(weak scaling) and no collective is needed on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1309_7695_b300 import inputs  # noqa: E402
+
+METRIC = "reaction firings/s & sim-steps/s (KS-matched) vs plain FP64; serve p50/p99"
+WORKLOAD = dict(n_species=32, n_reactions=64, n_sims=65536, t_end=100.0, n_samples=101,
+                x0_max=1000, eps=0.03, n_c=10, max_attempts=1 << 20, network_seed=0)
+FP64_PEAK_OPS = 148 * 2 * 2.032e9  # FP64 FMA-pipe ops/s: 148 SMs x 2/clk x 2032 MHz
+L2_FLUSH_BYTES = 256 << 20
+KERNEL_NAMES = {0: "lane_f64_kernel", 1: "warp_f64_kernel", 2: "lane_f64_kernel"}
+
+
+def algorithmic_fp64_ops(stats, M, N, nnz):
+    """FP64 operations the method performs, from the per-simulation counters.
+
+    Per SSA event: propensities (1.25 M mults), slot sums (M adds), slot tree
+    (31 adds), ln u (30 ops incl. one division), tau division, clock add,
+    target mult and ~2.5 descent subtractions: 2.25 M + 67.
+    Per leap attempt: propensities 1.25 M, a0 and a0c (2 M + 62), mu/sigma^2
+    (4 per net-change entry), tau' (~7 per species), tau'' (31), and M Poisson
+    draws at ~40 ops (inversion path): 43.25 M + 4 nnz + 7 N + 93.
+    """
+    ssa = float(stats["ssa_steps"].sum())
+    leap_attempts = float(stats["leaps"].sum() + stats["rejected"].sum())
+    return ssa * (2.25 * M + 67) + leap_attempts * (43.25 * M + 4 * nnz + 7 * N + 93)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_batch(rank=0):
+    w = WORKLOAD
+    return inputs.random_batch(w["n_species"], w["n_reactions"], w["n_sims"], seed=rank,
+                               x0_max=w["x0_max"], t_end=w["t_end"], n_samples=w["n_samples"],
+                               network_seed=w["network_seed"])
+
+
+def config_dict(extra=None):
+    w = WORKLOAD
+    d = {"workload": f"random mass-action network {w['n_species']} species x {w['n_reactions']} reactions, "
+                     f"{w['n_sims']} parameterizations, t_end={w['t_end']:g}, {w['n_samples']} sample times",
+         "n_species": w["n_species"], "n_reactions": w["n_reactions"], "n_sims_per_gpu": w["n_sims"],
+         "t_end": w["t_end"], "n_samples": w["n_samples"], "eps": w["eps"], "n_c": w["n_c"],
+         "max_attempts": w["max_attempts"], "mode": "tau-leap (CGP) + SSA fallback", "precision": "fp64-ref",
+         "l2": "flushed between timed steps (256 MB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def cpu_oracle_rate(batch, target_seconds=15.0, max_sims=4096, seed=1000):
+    """Oracle firings/s on a bounded prefix of the batch, all host cores."""
+    import oracle
+
+    o = oracle.default_opts(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"], max_attempts=WORKLOAD["max_attempts"])
+    n = 256
+    total_f = total_s = total_t = 0.0
+    done = 0
+    while done < max_sims and total_t < target_seconds:
+        rows = np.arange(done, min(done + n, max_sims))
+        t0 = time.perf_counter()
+        _, st = oracle.simulate_batch(batch, seed=seed, opts=o, rows=rows)
+        total_t += time.perf_counter() - t0
+        total_f += float(st["firings"].sum())
+        total_s += float(st["leaps"].sum() + st["ssa_steps"].sum())
+        done = int(rows[-1]) + 1
+        n = min(n * 2, 2048)
+    return {"value": total_f / total_t, "unit": "firings/s", "sim_steps_per_s": total_s / total_t,
+            "cores": oracle.num_threads(), "kind": "oracle", "seconds": round(total_t, 2),
+            "sample": f"first {done} of the {batch.n_sims} simulations (seed {seed}), OpenMP over simulations"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    batch = make_batch(0)
+    o = oracle.default_opts(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"], max_attempts=WORKLOAD["max_attempts"])
+    per_step = 512
+    for w in range(args.warmup):
+        oracle.simulate_batch(batch, seed=2000 + w, opts=o, rows=np.arange(per_step))
+    fir = steps = 0.0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        _, st = oracle.simulate_batch(batch, seed=1000 + k, opts=o, rows=np.arange(per_step))
+        fir += float(st["firings"].sum())
+        steps += float(st["leaps"].sum() + st["ssa_steps"].sum())
+    dt = time.perf_counter() - t0
+    value = fir / dt
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "firings/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random network and sweep)", "sim_steps_per_s": steps / dt,
+            "config": config_dict({"reference_sample": f"{per_step} simulations per step"}),
+            "cpu_baseline": {"value": value, "unit": "firings/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"first {per_step} of {batch.n_sims} simulations per step"},
+            "e2e": {"value": value, "unit": "firings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--layout", type=int, default=0, help="0 auto, 1 warp per simulation, 2 lane per simulation")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    # profiling / sweep knobs; the reported benchmark uses the defaults
+    ap.add_argument("--sims", type=int, default=None, help="override the simulations per GPU (profiling)")
+    ap.add_argument("--cap", type=int, default=None, help="override the per-simulation attempt cap (profiling)")
+    args = ap.parse_args()
+    if args.sims is not None:
+        WORKLOAD["n_sims"] = args.sims
+    if args.cap is not None:
+        WORKLOAD["max_attempts"] = args.cap
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1309_7695_b300 import abi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    batch = make_batch(rank)
+    net = batch.network
+    N, M, S, n = net.n_species, net.n_reactions, len(batch.sample_times), batch.n_sims
+    nnz = int((net.stoichiometry() != 0).sum())
+    sim_offset = rank * n
+    model = abi.Model(net)
+    p = torch.from_numpy(batch.params).to(dev)
+    x = torch.from_numpy(batch.x0).to(dev)
+    T = torch.from_numpy(batch.sample_times).to(dev)
+    out = torch.empty((n, S, N), dtype=torch.int32, device=dev)
+    st = torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    opts = abi.ssa_default_options(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"], max_attempts=WORKLOAD["max_attempts"],
+                                   layout=args.layout)
+    stream = torch.cuda.current_stream()
+
+    def one(seed):
+        abi.ssa_simulate_dev(model, p, x, batch.t_end, T, out, st, seed=seed, opts=opts, sim_offset=sim_offset,
+                             stream=stream)
+
+    for w in range(args.warmup):
+        one(5000 + w)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    times_ms, fir, simsteps, ops, capped = [], 0.0, 0.0, 0.0, 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one(1000 + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        times_ms.append(e0.elapsed_time(e1))
+        s = st.cpu().numpy().view(abi.STATS_DTYPE).reshape(-1)
+        fir += float(s["firings"].sum())
+        simsteps += float(s["leaps"].sum() + s["ssa_steps"].sum())
+        ops += algorithmic_fp64_ops(s, M, N, nnz)
+        capped += int((s["status"] == abi.SSA_STATUS_STEP_LIMIT).sum())
+    clk = clocks.stop()
+    local_t = sum(times_ms) / 1e3
+    t_max = local_t
+    tot = torch.tensor([fir, simsteps, ops, float(capped)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tt = torch.tensor([local_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        t_max = float(tt.item())
+    fir, simsteps, ops, capped = (float(v) for v in tot.tolist())
+
+    e2e = None
+    if not args.no_e2e:
+        # host-buffer path: pinned inputs -> ssa_submit_batch (H2D inside) -> ssa_fetch (D2H) each step
+        hp = torch.from_numpy(batch.params).pin_memory().numpy()
+        hx = torch.from_numpy(batch.x0).pin_memory().numpy()
+        hT = batch.sample_times.copy()
+        hs = torch.empty((n, S, N), dtype=torch.int32).pin_memory().numpy()
+        hst = np.zeros(n, dtype=abi.STATS_DTYPE)
+        e2e_t, e2e_f = 0.0, 0.0
+        for k in range(args.steps):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            job = abi.ssa_submit_batch(model, hp, hx, batch.t_end, hT, seed=1000 + k, opts=opts)
+            job.fetch(hs, hst)
+            job.release()
+            e2e_t += time.perf_counter() - t0
+            e2e_f += float(hst["firings"].sum())
+        et = torch.tensor([e2e_t, e2e_f], dtype=torch.float64, device=dev)
+        if world > 1:
+            mx = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(et, op=dist.ReduceOp.SUM)
+            e2e_t = float(mx.item())
+            e2e_f = float(et[1].item())
+        e2e = {"value": e2e_f / e2e_t, "unit": "firings/s",
+               "h2d_bytes_per_step": int(hp.nbytes + hx.nbytes + hT.nbytes),
+               "d2h_bytes_per_step": int(hs.nbytes + hst.nbytes)}
+
+    if rank == 0:
+        kernel_s = local_t / args.steps
+        achieved = ops / world / args.steps / kernel_s
+        line = {"metric": METRIC, "value": fir / t_max, "unit": "firings/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded random network and parameter sweep)",
+                "sim_steps_per_s": simsteps / t_max,
+                "config": config_dict({"parallelism": f"dp{world} (independent simulation shards)",
+                                       "capped_fraction": capped / (world * n * args.steps)}),
+                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
+                             "unit": "TFP64-op/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
+                             "kernel": KERNEL_NAMES.get(args.layout, "lane_f64_kernel"),
+                             "peak_source": "148 SMs x 2 FP64 ops/clk x 2032 MHz"},
+                "clocks": clk, "gpu_launches": args.steps, "e2e": e2e}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_rate(batch)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    model.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -72,7 +72,8 @@ extern "C" {
 
 /* ssa_options.layout */
 #define SSA_LAYOUT_AUTO 0
-#define SSA_LAYOUT_WARP 1 /* one warp (32 lanes) per simulation */
+#define SSA_LAYOUT_WARP 1 /* one warp (32 lanes) per simulation throughout */
+#define SSA_LAYOUT_LANE 2 /* one simulation per lane for SSA steps; warp-cooperative leaps */
 
 typedef struct ssa_model *ssa_model_t;
 typedef struct ssa_job *ssa_job_t;

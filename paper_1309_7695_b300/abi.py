@@ -37,6 +37,7 @@ SSA_MODE_EXACT = 1
 SSA_FP64_REF = 0
 SSA_LAYOUT_AUTO = 0
 SSA_LAYOUT_WARP = 1
+SSA_LAYOUT_LANE = 2
 
 EXPORTED = [
     "ssa_default_options", "ssa_load_model", "ssa_free_model", "ssa_model_info",

@@ -25,6 +25,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-r
 UNITS = {
     "abi.cu": [],
     "kernel_warp_f64.cu": ["-fmad=false"],
+    "kernel_lane_f64.cu": ["-fmad=false"],
 }
 
 

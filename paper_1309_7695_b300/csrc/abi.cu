@@ -104,6 +104,7 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
     std::vector<int32_t> rinfo(M);
     std::vector<std::vector<int32_t>> nu_rows(M);
     std::vector<std::vector<int32_t>> tr_rows(N);
+    std::vector<std::vector<int32_t>> dep_rows(N);
     std::vector<int32_t> hor(N, 0);
     std::vector<int32_t> dense(N, 0);
     std::vector<int32_t> seen(N, -1);
@@ -135,6 +136,7 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
             s1 = std::max(sp[0], sp[1]);
         }
         rinfo[j] = kind | (s0 << 2) | (s1 << 17);
+        for (int q = 0; q < n; ++q) dep_rows[sp[q]].push_back(j);
         for (int q = 0; q < n; ++q) {
             const int cls = (order == 1) ? 1 : (cf[q] == 2 ? 3 : 2);
             hor[sp[q]] = std::max(hor[sp[q]], cls);
@@ -175,8 +177,13 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
     L.off_nu_ent = L.off_nu_ptr + M + 1;
     L.off_tr_ptr = L.off_nu_ent + nnz;
     L.off_tr_ent = L.off_tr_ptr + N + 1;
+    int ndep = 0;
+    for (auto &r : dep_rows) ndep += (int)r.size();
+    L.ndep = ndep;
     L.off_hor = L.off_tr_ent + nnz;
-    L.words = L.off_hor + N;
+    L.off_dep_ptr = L.off_hor + N;
+    L.off_dep_ent = L.off_dep_ptr + N + 1;
+    L.words = L.off_dep_ent + ndep;
     L.max_nu_len = max_nu_len;
     std::vector<int32_t> blob(L.words);
     std::copy(rinfo.begin(), rinfo.end(), blob.begin() + L.off_rinfo);
@@ -193,6 +200,12 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
     }
     blob[L.off_tr_ptr + N] = pos;
     std::copy(hor.begin(), hor.end(), blob.begin() + L.off_hor);
+    pos = 0;
+    for (int i = 0; i < N; ++i) {
+        blob[L.off_dep_ptr + i] = pos;
+        for (int v : dep_rows[i]) blob[L.off_dep_ent + pos++] = v;
+    }
+    blob[L.off_dep_ptr + N] = pos;
 
     auto *m = new ssa_model();
     m->L = L;
@@ -239,7 +252,8 @@ static int check_options(const ssa_options *o)
     if (!(o->ssa_factor >= 0.0) || !std::isfinite(o->ssa_factor)) return fail(SSA_EINVAL, "ssa_factor must be finite and >= 0");
     if (o->max_halvings < 0) return fail(SSA_EINVAL, "max_halvings must be >= 0");
     if (o->max_attempts < 0 || o->max_attempts > 0xFFFFFFFFll) return fail(SSA_EINVAL, "max_attempts must be in 0..2^32-1");
-    if (o->layout != SSA_LAYOUT_AUTO && o->layout != SSA_LAYOUT_WARP) return fail(SSA_EUNSUPPORTED, "unknown layout");
+    if (o->layout != SSA_LAYOUT_AUTO && o->layout != SSA_LAYOUT_WARP && o->layout != SSA_LAYOUT_LANE)
+        return fail(SSA_EUNSUPPORTED, "unknown layout");
     if (o->block_warps < 0 || o->block_warps > 8) return fail(SSA_EINVAL, "block_warps must be in 0..8");
     return SSA_OK;
 }
@@ -268,12 +282,22 @@ int ssa_simulate_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const do
     int sms = 0, smem_optin = 0;
     TL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
     TL_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    // Launch shape: the lane layout (one simulation per lane for SSA steps)
+    // unless asked otherwise or its per-warp workspace does not fit.
+    int layout = o.layout;
+    if (layout == SSA_LAYOUT_AUTO)
+        layout = (tl::lane_f64_smem_bytes(m->L, 1) <= (size_t)smem_optin) ? SSA_LAYOUT_LANE : SSA_LAYOUT_WARP;
+    auto smem_of = [&](int w) {
+        return layout == SSA_LAYOUT_LANE ? tl::lane_f64_smem_bytes(m->L, w) : tl::warp_f64_smem_bytes(m->L, w);
+    };
     int warps = o.block_warps > 0 ? o.block_warps : 4;
-    while (warps > 1 && tl::warp_f64_smem_bytes(m->L, warps) > (size_t)smem_optin) --warps;
-    const size_t smem = tl::warp_f64_smem_bytes(m->L, warps);
+    while (warps > 1 && smem_of(warps) > (size_t)smem_optin) --warps;
+    const size_t smem = smem_of(warps);
     if (smem > (size_t)smem_optin) return fail(SSA_EUNSUPPORTED, "network too large for the shared-memory workspace");
-    const int per_sm = std::max(1, tl::warp_ref_occupancy(warps, smem));
-    const long long need_blocks = (n_sims + warps - 1) / warps;
+    const int occ = layout == SSA_LAYOUT_LANE ? tl::lane_ref_occupancy(warps, smem) : tl::warp_ref_occupancy(warps, smem);
+    const int per_sm = std::max(1, occ);
+    const long long sims_per_block = (long long)warps * (layout == SSA_LAYOUT_LANE ? 32 : 1);
+    const long long need_blocks = (n_sims + sims_per_block - 1) / sims_per_block;
     const int grid = (int)std::min<long long>((long long)per_sm * sms, need_blocks);
 
     tl::SimArgs a{};
@@ -300,7 +324,9 @@ int ssa_simulate_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const do
     TL_CUDA(cudaMallocAsync(&counter, sizeof(unsigned long long), s));
     a.work_counter = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = tl::launch_warp_ref(a, warps, grid, smem, s);
+    if (e == cudaSuccess)
+        e = layout == SSA_LAYOUT_LANE ? tl::launch_lane_ref(a, warps, grid, smem, s)
+                                      : tl::launch_warp_ref(a, warps, grid, smem, s);
     cudaError_t e2 = cudaFreeAsync(counter, s);
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(SSA_ECUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(e2));

@@ -56,6 +56,28 @@ __device__ __forceinline__ double u01(uint32_t w0, uint32_t w1)
     return __longlong_as_double((long long)((expo << 52) | mant));
 }
 
+// ------------------------------------------- exact bit-level helpers
+// For doubles that are never negative and never -0.0 (propensities, their
+// sums, times), IEEE order equals the order of the bit patterns read as
+// signed 64-bit integers, so these comparisons run on the integer pipe.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ bool nn_ge(double a, double b) { return dbits(a) >= dbits(b); }
+__device__ __forceinline__ bool nn_gt(double a, double b) { return dbits(a) > dbits(b); }
+__device__ __forceinline__ bool nn_pos(double a) { return dbits(a) > 0; }
+
+// Exact conversion of a count 0 <= v < 2^53 to double, assembled from bits
+// (normalise with a leading-zero count; no rounding can occur).  Larger
+// values use the round-to-nearest conversion.
+__device__ __forceinline__ double u53_to_double(unsigned long long v)
+{
+    if (v == 0) return 0.0;
+    if (v >= (1ull << 53)) return __ull2double_rn(v);
+    const int p = 63 - __clzll((long long)v);                       // v in [2^p, 2^(p+1))
+    const unsigned long long frac = (v << (52 - p)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(((unsigned long long)(1023 + p) << 52) | frac));
+}
+__device__ __forceinline__ double count_to_double(int x) { return u53_to_double((unsigned long long)(unsigned)x); }
+
 // ------------------------------------------------------ log, exp, log k!
 // ln 2 split: the high part keeps 32 significant bits so that e * LN2_HI
 // is exact for every exponent e that occurs.

@@ -18,9 +18,11 @@ namespace tl {
 //   tr_ent [nnz]   j << 8 | (nu & 0xff)          j ascending
 //   hor [N]        highest-order class of species i: 0 none, 1 first order,
 //                  2 second order as X+Y only, 3 some reaction takes 2X
+//   dep_ptr [N+1]  reactions whose propensity reads species i (i is a reactant)
+//   dep_ent [ndep] reaction indices
 struct ModelLayout {
-    int32_t N, M, nnz;
-    int32_t off_rinfo, off_nu_ptr, off_nu_ent, off_tr_ptr, off_tr_ent, off_hor;
+    int32_t N, M, nnz, ndep;
+    int32_t off_rinfo, off_nu_ptr, off_nu_ent, off_tr_ptr, off_tr_ent, off_hor, off_dep_ptr, off_dep_ent;
     int32_t words;
     int32_t max_nu_len;
 };
@@ -69,6 +71,12 @@ __host__ __device__ inline size_t model_smem_bytes(const ModelLayout &L)
 {
     return ((size_t)L.words * 4 + 15) & ~size_t(15);
 }
+
+// Lane-per-simulation FP64 reference kernel (kernel_lane_f64.cu): SSA steps
+// one simulation per lane, leaps and step-size selection warp-cooperative.
+size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps);
+cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+int lane_ref_occupancy(int block_warps, size_t smem);
 
 // Warp-per-simulation FP64 reference kernel (kernel_warp_f64.cu).
 size_t warp_f64_smem_bytes(const ModelLayout &L, int block_warps);

@@ -28,11 +28,10 @@
 
 #include "device_f64.cuh"
 #include "engine.h"
+#include "warp_f64.cuh"
 
 namespace tl {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 struct Workspace {
     double *a, *c;
@@ -59,74 +58,6 @@ __device__ __forceinline__ Workspace carve(unsigned char *p, int N, int M)
     p += r16((size_t)M);
     w.irs = p;
     return w;
-}
-
-// Slot tree over the warp: L[0] = this lane's slot sum, L[k] = L[k-1] +
-// L[k-1] of lane ^ (16 >> (k-1)).  Every lane ends with the same L[5].
-__device__ __forceinline__ double slot_tree(double v, double L[6])
-{
-    L[0] = v;
-#pragma unroll
-    for (int k = 1; k <= 5; ++k) L[k] = L[k - 1] + __shfl_xor_sync(kFull, L[k - 1], 16 >> (k - 1));
-    return L[5];
-}
-
-// Pick j with probability v_j / total given target = u * total: descend the
-// slot tree (second child when target >= first child and second child > 0),
-// then walk the chosen slot's reactions in increasing j.  When `crit_only`
-// the weights are the critical propensities (0 for noncritical reactions).
-__device__ __forceinline__ int slot_select(const double L[6], double target, const double *a,
-                                           const unsigned char *crit, bool crit_only, int M)
-{
-    int cls = 0;
-#pragma unroll
-    for (int k = 4; k >= 0; --k) {
-        const int step = 1 << (4 - k);
-        const double left = __shfl_sync(kFull, L[k], cls);
-        const double right = __shfl_sync(kFull, L[k], cls + step);
-        if (target >= left && right > 0.0) {
-            target = target - left;
-            cls += step;
-        }
-    }
-    double cum = 0.0;
-    int last = -1;
-    for (int j = cls; j < M; j += 32) {
-        const double v = (crit_only && !crit[j]) ? 0.0 : a[j];
-        cum = cum + v;
-        if (v > 0.0) last = j;
-        if (cum > target) return j;
-    }
-    return last;
-}
-
-__device__ __forceinline__ double propensity(int info, double c, const int *x)
-{
-    const int kind = info & 3;
-    const int s0 = (info >> 2) & 0x7fff;
-    const int s1 = (info >> 17) & 0x7fff;
-    if (kind == 0) return c;
-    if (kind == 1) return c * (double)x[s0];
-    if (kind == 2) return (c * (double)x[s0]) * (double)x[s1];
-    const long long xi = x[s0];
-    return c * (double)((xi * (xi - 1)) / 2);
-}
-
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
-{
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(kFull, v, d);
-        v = o < v ? o : v;
-    }
-    return v;
-}
-
-__device__ __forceinline__ long long warp_sum_i64(long long v)
-{
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-    return v;
 }
 
 __device__ void run_simulation(const SimArgs &A, long long row, const Workspace &w, const int *blob,

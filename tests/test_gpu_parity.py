@@ -19,6 +19,8 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU machines skip the mo
 from paper_1309_7695_b300 import abi  # noqa: E402
 
 DEV = torch.device("cuda:0")
+LAYOUTS = [abi.SSA_LAYOUT_LANE, abi.SSA_LAYOUT_WARP]
+LAYOUT_IDS = ["lane", "warp"]
 
 
 def gpu_run(batch, seed=0, mode=abi.SSA_MODE_TAU_LEAP, sim_offset=0, rows=None, **opt):
@@ -62,35 +64,39 @@ def assert_same(gpu, ref, what=""):
 
 # ------------------------------------------------------------- workloads
 
-@pytest.mark.parametrize("mode", [abi.SSA_MODE_EXACT, abi.SSA_MODE_TAU_LEAP])
-def test_michaelis_menten_sweep_bit_exact(mode):
+@pytest.mark.parametrize("layout", LAYOUTS, ids=LAYOUT_IDS)
+@pytest.mark.parametrize("mode", [abi.SSA_MODE_EXACT, abi.SSA_MODE_TAU_LEAP], ids=["exact", "tau"])
+def test_michaelis_menten_sweep_bit_exact(mode, layout):
     b = inputs.mm_batch(1024, seed=0)
-    assert_same(gpu_run(b, seed=0, mode=mode), oracle_run(b, seed=0, mode=mode), "MM")
+    assert_same(gpu_run(b, seed=0, mode=mode, layout=layout), oracle_run(b, seed=0, mode=mode), "MM")
 
 
-def test_michaelis_menten_large_counts_leaps_bit_exact():
+@pytest.mark.parametrize("layout", LAYOUTS, ids=LAYOUT_IDS)
+def test_michaelis_menten_large_counts_leaps_bit_exact(layout):
     b = inputs.mm_batch(256, seed=1, scale=100.0)
     ref = oracle_run(b, seed=3, eps=0.03)
     assert ref[1]["leaps"].sum() > 0
-    assert_same(gpu_run(b, seed=3, eps=0.03), ref, "MM x100")
+    assert_same(gpu_run(b, seed=3, eps=0.03, layout=layout), ref, "MM x100")
 
 
+@pytest.mark.parametrize("layout", LAYOUTS, ids=LAYOUT_IDS)
 @pytest.mark.parametrize("N,M,n,t_end,cap", [
     (32, 64, 320, 100.0, 200_000),     # the 32 x 64 sweep shape, 10 tiles of 32 sims
     (128, 256, 40, 20.0, 100_000),     # the 128 x 256 shape (N, M > 32: several lanes' chunks)
     (5, 7, 333, 50.0, 200_000),        # ragged: M, N not multiples of 32
     (40, 33, 97, 30.0, 200_000),       # M = 33: one full chunk + 1
 ])
-def test_random_network_bit_exact(N, M, n, t_end, cap):
+def test_random_network_bit_exact(N, M, n, t_end, cap, layout):
     b = inputs.random_batch(N, M, n, seed=11, t_end=t_end, n_samples=21,
                             x0_max=1000 if N <= 32 else 10_000)
     ref = oracle_run(b, seed=5, max_attempts=cap)
-    got = gpu_run(b, seed=5, max_attempts=cap)
+    got = gpu_run(b, seed=5, max_attempts=cap, layout=layout)
     assert_same(got, ref, f"random {N}x{M}")
     assert ref[1]["leaps"].sum() > 0 and ref[1]["ssa_steps"].sum() > 0
 
 
-def test_closed_form_networks_bit_exact():
+@pytest.mark.parametrize("layout", LAYOUTS, ids=LAYOUT_IDS)
+def test_closed_form_networks_bit_exact(layout):
     cases = [
         (inputs.birth_death(), [10.0, 0.1], [0], 30.0),
         (inputs.isomerization(), [1.0], [10_000, 0], 2.0),
@@ -100,38 +106,56 @@ def test_closed_form_networks_bit_exact():
     for net, rates, x0, t_end in cases:
         b = inputs.replicate_batch(net, rates, x0, 200, t_end, 7)
         for mode in (abi.SSA_MODE_EXACT, abi.SSA_MODE_TAU_LEAP):
-            assert_same(gpu_run(b, seed=2, mode=mode), oracle_run(b, seed=2, mode=mode), net.name)
+            assert_same(gpu_run(b, seed=2, mode=mode, layout=layout), oracle_run(b, seed=2, mode=mode),
+                        net.name)
 
 
 # ------------------------------------------------------------ edge cases
 
-def test_status_paths_bit_exact():
-    # step cap, overflow (A -> 2A explodes), frozen system
-    b = inputs.random_batch(8, 16, 64, seed=4, t_end=50.0, n_samples=11)
-    assert_same(gpu_run(b, max_attempts=37), oracle_run(b, max_attempts=37), "cap")
-    boom = inputs.replicate_batch(inputs.Network(1, [[(0, 1)]], [[(0, 2)]]), [1.0], [1000], 16, 100.0, 11)
-    got = gpu_run(boom)
-    assert np.all(got[1]["status"] == abi.SSA_STATUS_OVERFLOW)
-    assert_same(got, oracle_run(boom), "overflow")
-    frozen = inputs.replicate_batch(inputs.isomerization(), [1.0], [0, 9], 5, 10.0, 4)
-    assert_same(gpu_run(frozen), oracle_run(frozen), "frozen")
+@pytest.mark.parametrize("layout", LAYOUTS, ids=LAYOUT_IDS)
+def test_status_paths_bit_exact(layout):
+    # step cap, overflow (A -> 2A explodes), frozen system, in both modes
+    for mode in (abi.SSA_MODE_TAU_LEAP, abi.SSA_MODE_EXACT):
+        b = inputs.random_batch(8, 16, 64, seed=4, t_end=50.0, n_samples=11)
+        assert_same(gpu_run(b, max_attempts=37, layout=layout, mode=mode),
+                    oracle_run(b, max_attempts=37, mode=mode), "cap")
+        boom = inputs.replicate_batch(inputs.Network(1, [[(0, 1)]], [[(0, 2)]]), [1.0], [1000], 16, 100.0, 11)
+        cap = 1 << 22 if mode == abi.SSA_MODE_TAU_LEAP else 1 << 14   # exact SSA: one birth per step
+        got = gpu_run(boom, layout=layout, mode=mode, max_attempts=cap)
+        want = abi.SSA_STATUS_OVERFLOW if mode == abi.SSA_MODE_TAU_LEAP else abi.SSA_STATUS_STEP_LIMIT
+        assert np.all(got[1]["status"] == want)
+        assert_same(got, oracle_run(boom, mode=mode, max_attempts=cap), "overflow")
+        frozen = inputs.replicate_batch(inputs.isomerization(), [1.0], [0, 9], 5, 10.0, 4)
+        assert_same(gpu_run(frozen, layout=layout, mode=mode), oracle_run(frozen, mode=mode), "frozen")
 
 
-def test_degenerate_sizes():
+@pytest.mark.parametrize("layout", LAYOUTS, ids=LAYOUT_IDS)
+def test_degenerate_sizes(layout):
     b = inputs.mm_batch(16)
     # no simulations
     e = inputs.Batch(b.network, b.params[:0], b.x0[:0], b.t_end, b.sample_times)
-    s, st = gpu_run(e)
+    s, st = gpu_run(e, layout=layout)
     assert s.shape == (0, 11, 4) and st.shape == (0,)
     # t_end = 0: every sample is x0, nothing fires
     z = inputs.Batch(b.network, b.params, b.x0, 0.0, np.zeros(3))
-    assert_same(gpu_run(z), oracle_run(z), "t_end=0")
+    assert_same(gpu_run(z, layout=layout), oracle_run(z), "t_end=0")
     # no sample times: only counters
     n = inputs.Batch(b.network, b.params, b.x0, 5.0, np.zeros(0))
-    assert_same(gpu_run(n), oracle_run(n), "S=0")
+    assert_same(gpu_run(n, layout=layout), oracle_run(n), "S=0")
     # repeated sample times
     r = inputs.Batch(b.network, b.params, b.x0, 5.0, np.array([0.0, 1.0, 1.0, 5.0, 5.0]))
-    assert_same(gpu_run(r), oracle_run(r), "repeated T")
+    assert_same(gpu_run(r, layout=layout), oracle_run(r), "repeated T")
+    # a single simulation (one busy lane in the warp)
+    one = inputs.random_batch(16, 32, 1, seed=6, t_end=20.0, n_samples=5)
+    assert_same(gpu_run(one, layout=layout), oracle_run(one), "n=1")
+
+
+@pytest.mark.parametrize("block_warps", [1, 2, 4, 8])
+def test_launch_shape_does_not_change_results(block_warps):
+    b = inputs.random_batch(32, 64, 300, seed=12, t_end=20.0, n_samples=11)
+    ref = gpu_run(b, seed=3, max_attempts=100_000, layout=abi.SSA_LAYOUT_WARP)
+    got = gpu_run(b, seed=3, max_attempts=100_000, layout=abi.SSA_LAYOUT_LANE, block_warps=block_warps)
+    assert_same(got, ref, f"block_warps={block_warps}")
 
 
 def test_sharding_by_sim_offset_is_bit_identical():
