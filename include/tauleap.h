@@ -151,6 +151,25 @@ int ssa_simulate_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
                      const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
                      void *stream);
 
+/* Same as ssa_simulate_dev, for callers that cannot allocate device memory
+ * (for example code that runs inside an allocator's callbacks, or programs
+ * that reserve all device memory up front).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The one piece of scratch memory the
+ * kernel needs, its 8-byte work counter, lives in a 256-byte static device
+ * array that every GPU loading this library keeps until process exit; a
+ * launch needing more scratch than that is rejected with SSA_EINVAL.  The
+ * first call on each device looks up the array's device address, so make
+ * that first call before any stream capture.  All calls share the array: the
+ * counter is cleared on `stream` before each launch, and calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * it and must be serialised by the caller.  The paper has no counterpart to
+ * this entry point. */
+int ssa_simulate_dev_noalloc(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
+                             const double *params, const int32_t *x0, double t_end,
+                             const double *sample_times, int32_t n_samples, uint64_t seed,
+                             const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
+                             void *stream);
+
 /* Host-buffer form.  Copies the HOST inputs to device memory that the job
  * owns and enqueues the simulation on `stream` (NULL = a stream the job
  * creates).  The inputs may be reused once this returns.  Fails with

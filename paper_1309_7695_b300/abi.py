@@ -41,7 +41,7 @@ SSA_LAYOUT_LANE = 2
 
 EXPORTED = [
     "ssa_default_options", "ssa_load_model", "ssa_free_model", "ssa_model_info",
-    "ssa_simulate_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
+    "ssa_simulate_dev", "ssa_simulate_dev_noalloc", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
     "ssa_release_job", "ssa_last_error", "ssa_abi_version",
 ]
 
@@ -94,6 +94,7 @@ def lib():
     L.ssa_free_model.argtypes = [vp]
     L.ssa_model_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.ssa_simulate_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp, vp, vp]
+    L.ssa_simulate_dev_noalloc.argtypes = L.ssa_simulate_dev.argtypes
     L.ssa_submit_batch.argtypes = [vp, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp,
                                    ctypes.POINTER(vp)]
     L.ssa_poll.argtypes = [vp, ctypes.POINTER(i32)]
@@ -179,6 +180,23 @@ def ssa_simulate_dev(model: Model, params, x0, t_end, sample_times, samples, sta
     _check(lib().ssa_simulate_dev(model.handle, n, int(sim_offset), _ptr(params), _ptr(x0), float(t_end),
                                   _ptr(sample_times), int(sample_times.numel()), int(seed), ctypes.byref(o),
                                   _ptr(samples), _ptr(stats), ctypes.c_void_p(int(handle))))
+
+
+def ssa_simulate_dev_noalloc(model: Model, params, x0, t_end, sample_times, samples, stats=None, seed=0,
+                             opts=None, sim_offset=0, stream=None):
+    """Like ssa_simulate_dev, but the library allocates nothing: its work
+    counter lives in a static device array shared by all calls (calls that
+    overlap on the GPU race on it)."""
+    n = int(params.shape[0]) if params.dim() == 2 else 0
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    o = opts if opts is not None else ssa_default_options()
+    _check(lib().ssa_simulate_dev_noalloc(model.handle, n, int(sim_offset), _ptr(params), _ptr(x0), float(t_end),
+                                          _ptr(sample_times), int(sample_times.numel()), int(seed),
+                                          ctypes.byref(o), _ptr(samples), _ptr(stats),
+                                          ctypes.c_void_p(int(handle))))
 
 
 class Job:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -258,12 +259,18 @@ static int check_options(const ssa_options *o)
     return SSA_OK;
 }
 
-int ssa_simulate_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
-                     const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
-                     uint64_t seed, const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
-                     void *stream)
+}  // extern "C"
+
+namespace {
+
+// Validation, launch-shape choice and launch shared by the device-pointer
+// entry points.  `counter` is the caller-provided work counter (zeroed on
+// `stream` before the launch) or nullptr to allocate a stream-ordered one.
+int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
+                      const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
+                      uint64_t seed, const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
+                      void *stream, unsigned long long *counter_in)
 {
-    g_error.clear();
     if (!m) return fail(SSA_EINVAL, "null model");
     ssa_options o;
     if (opts) o = *opts;
@@ -278,7 +285,6 @@ int ssa_simulate_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const do
     DeviceGuard g(m->device);
     if (!g.ok) return fail(SSA_ECUDA, "cannot select the model's device");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-
     int sms = 0, smem_optin = 0;
     TL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
     TL_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
@@ -320,18 +326,72 @@ int ssa_simulate_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const do
     a.max_attempts = o.max_attempts;
     a.samples = samples;
     a.stats = stats;
-    void *counter = nullptr;
-    TL_CUDA(cudaMallocAsync(&counter, sizeof(unsigned long long), s));
+    void *counter = counter_in;
+    if (!counter_in) TL_CUDA(cudaMallocAsync(&counter, sizeof(unsigned long long), s));
     a.work_counter = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
         e = layout == SSA_LAYOUT_LANE ? tl::launch_lane_ref(a, warps, grid, smem, s)
                                       : tl::launch_warp_ref(a, warps, grid, smem, s);
-    cudaError_t e2 = cudaFreeAsync(counter, s);
+    cudaError_t e2 = counter_in ? cudaSuccess : cudaFreeAsync(counter, s);
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(SSA_ECUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(e2));
     return SSA_OK;
 }
+
+
+// ---------------------------------------------------------------------
+// Allocation-free launch path (ssa_simulate_dev_noalloc).
+//
+// The simulation kernels need one piece of scratch memory besides their
+// inputs and outputs: the 8-byte work counter from which warps take
+// simulation indices.  ssa_simulate_dev allocates it per call with
+// cudaMallocAsync.  Callers that may not allocate device memory (code
+// running where allocation is forbidden or would deadlock, such as a custom
+// allocator's own callbacks, or programs that reserve all device memory up
+// front) use the variant below, whose counter lives in this file-scope
+// array instead.  Every GPU that loads the library holds these 256 bytes
+// until the process exits.  In host code the symbol is only a host-side
+// stand-in, so its device address is looked up once per device with
+// cudaGetSymbolAddress and passed to the kernel.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[32];
+constexpr size_t kNoallocScratchBytes = sizeof(g_noalloc_scratch);
+constexpr size_t kNoallocCounterBytes = sizeof(unsigned long long);
+
+std::mutex g_noalloc_mutex;
+unsigned long long *g_noalloc_addr[256] = {nullptr};
+
+// Device address of the static scratch on the current device (looked up on
+// the first call per device).
+int noalloc_scratch(int device, unsigned long long **out)
+{
+    if (device < 0 || device >= 256) return fail(SSA_EUNSUPPORTED, "device ordinal above 255");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return fail(SSA_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_addr[device] = static_cast<unsigned long long *>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return SSA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ssa_simulate_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
+                     const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
+                     uint64_t seed, const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
+                     void *stream)
+{
+    g_error.clear();
+    return simulate_dev_impl(m, n_sims, sim_offset, params, x0, t_end, sample_times, n_samples, seed, opts,
+                             samples, stats, stream, nullptr);
+}
+
 
 static void job_free_buffers(ssa_job *j)
 {
@@ -488,4 +548,23 @@ int ssa_release_job(ssa_job_t j)
     return SSA_OK;
 }
 
+int ssa_simulate_dev_noalloc(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
+                             const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
+                             uint64_t seed, const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
+                             void *stream)
+{
+    g_error.clear();
+    if (!m) return fail(SSA_EINVAL, "null model");
+    if (kNoallocCounterBytes > kNoallocScratchBytes)
+        return fail(SSA_EINVAL, "launch needs more scratch than the static array holds");
+    DeviceGuard g(m->device);
+    if (!g.ok) return fail(SSA_ECUDA, "cannot select the model's device");
+    unsigned long long *counter = nullptr;
+    int rc = noalloc_scratch(m->device, &counter);
+    if (rc) return rc;
+    return simulate_dev_impl(m, n_sims, sim_offset, params, x0, t_end, sample_times, n_samples, seed, opts,
+                             samples, stats, stream, counter);
+}
+
 }  // extern "C"
+
