@@ -69,6 +69,7 @@ extern "C" {
 
 /* ssa_options.precision */
 #define SSA_FP64_REF 0 /* bit-identical to the FP64 reference algorithm */
+#define SSA_FAST 1     /* FP32 propensities, Poisson means and sampler; FP64 clock, a0, tau' */
 
 /* ssa_options.layout */
 #define SSA_LAYOUT_AUTO 0
@@ -97,7 +98,7 @@ typedef struct {
 
 typedef struct {
     int32_t mode;         /* SSA_MODE_* (default TAU_LEAP) */
-    int32_t precision;    /* SSA_FP64_REF */
+    int32_t precision;    /* SSA_FP64_REF or SSA_FAST */
     double eps;           /* CGP error-control parameter epsilon (0.03) */
     int32_t n_c;          /* critical threshold: L_j < n_c (10) */
     int32_t ssa_block;    /* SSA steps per fallback block (100) */

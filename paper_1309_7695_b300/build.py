@@ -26,6 +26,7 @@ UNITS = {
     "abi.cu": [],
     "kernel_warp_f64.cu": ["-fmad=false"],
     "kernel_lane_f64.cu": ["-fmad=false"],
+    "kernel_lane_fast.cu": [],
 }
 
 

@@ -246,7 +246,9 @@ int ssa_model_info(ssa_model_t m, int32_t *n_species, int32_t *n_reactions)
 static int check_options(const ssa_options *o)
 {
     if (o->mode != SSA_MODE_TAU_LEAP && o->mode != SSA_MODE_EXACT) return fail(SSA_EINVAL, "unknown mode");
-    if (o->precision != SSA_FP64_REF) return fail(SSA_EUNSUPPORTED, "only SSA_FP64_REF precision is built");
+    if (o->precision != SSA_FP64_REF && o->precision != SSA_FAST) return fail(SSA_EINVAL, "unknown precision");
+    if (o->precision == SSA_FAST && o->layout == SSA_LAYOUT_WARP)
+        return fail(SSA_EUNSUPPORTED, "fast mode runs in the lane layout only");
     if (!(o->eps > 0.0) || !(o->eps < 1.0)) return fail(SSA_EINVAL, "eps must be in (0,1)");
     if (o->n_c < 0) return fail(SSA_EINVAL, "n_c must be >= 0");
     if (o->ssa_block < 1) return fail(SSA_EINVAL, "ssa_block must be >= 1");
@@ -300,7 +302,10 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     while (warps > 1 && smem_of(warps) > (size_t)smem_optin) --warps;
     const size_t smem = smem_of(warps);
     if (smem > (size_t)smem_optin) return fail(SSA_EUNSUPPORTED, "network too large for the shared-memory workspace");
-    const int occ = layout == SSA_LAYOUT_LANE ? tl::lane_ref_occupancy(warps, smem) : tl::warp_ref_occupancy(warps, smem);
+    const bool fast = (o.precision == SSA_FAST);
+    const int occ = layout == SSA_LAYOUT_LANE
+                        ? (fast ? tl::lane_fast_occupancy(warps, smem) : tl::lane_ref_occupancy(warps, smem))
+                        : tl::warp_ref_occupancy(warps, smem);
     const int per_sm = std::max(1, occ);
     const long long sims_per_block = (long long)warps * (layout == SSA_LAYOUT_LANE ? 32 : 1);
     const long long need_blocks = (n_sims + sims_per_block - 1) / sims_per_block;
@@ -331,7 +336,8 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     a.work_counter = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-        e = layout == SSA_LAYOUT_LANE ? tl::launch_lane_ref(a, warps, grid, smem, s)
+        e = layout == SSA_LAYOUT_LANE ? (fast ? tl::launch_lane_fast(a, warps, grid, smem, s)
+                                              : tl::launch_lane_ref(a, warps, grid, smem, s))
                                       : tl::launch_warp_ref(a, warps, grid, smem, s);
     cudaError_t e2 = counter_in ? cudaSuccess : cudaFreeAsync(counter, s);
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -77,6 +77,9 @@ __host__ __device__ inline size_t model_smem_bytes(const ModelLayout &L)
 size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps);
 cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
 int lane_ref_occupancy(int block_warps, size_t smem);
+// Fast-mode instantiation (kernel_lane_fast.cu), same shared-memory layout.
+cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+int lane_fast_occupancy(int block_warps, size_t smem);
 
 // Warp-per-simulation FP64 reference kernel (kernel_warp_f64.cu).
 size_t warp_f64_smem_bytes(const ModelLayout &L, int block_warps);

@@ -1,601 +1,43 @@
-// Lane-per-simulation kernel, FP64 reference mode.
+// FP64 reference instantiation of the lane-per-simulation kernel.
 //
-// Each lane of a warp owns one simulation (the paper's one thread per
-// simulation, Methods, last paragraph) for its exact SSA steps.  An SSA step
-// is mostly scalar work (ln u, tau = E/a0, a tree descent), so giving every
-// lane its own simulation keeps all 32 FP64 lanes busy instead of repeating
-// the same scalar on 32 lanes.  The step-size selection and the leaps,
-// which are O(M + N) vector work, run warp-cooperatively for one
-// simulation at a time.
-//
-// Per-simulation state in shared memory, one column per lane (row stride 33,
-// so both lane-local rows and one-column-across-lanes accesses are free of
-// bank conflicts):
-//   X [N][33]  int32   molecule counts
-//   V [63][33] double  the 32-slot tree of the propensities: nodes 0..31 are
-//                      the slot sums S_l = sum_c a_{32c+l} (increasing c),
-//                      level k nodes c < 32>>k are V_k[c] = V_{k-1}[c] +
-//                      V_{k-1}[c + (32>>k)], node 62 is a0.
-// After an SSA firing only the slots holding a reaction whose reactants
-// changed, and their ancestors, are recomputed; every node is always the sum
-// of its two children in the same order, so the tree equals a full
-// recomputation bit for bit.
-//
-// Per-lane control state (registers), a small state machine:
-//   NEED -> (take the next simulation index)  -> TOP
-//   TOP  -> (cooperative: record samples, propensities, critical set, a0c,
-//            tau'; then an SSA block, or one leap attempt and its retries)
-//        -> SSA | TOP | DONE
-//   SSA  -> (lane-local: one SSA step per warp iteration) -> SSA | TOP | DONE
-//   DONE -> (record the remaining samples, write the counters) -> NEED
-// In exact-SSA mode TOP is lane-local too.
-#include <climits>
-
-#include "device_f64.cuh"
-#include "engine.h"
-#include "warp_f64.cuh"
+// Compiled with -fmad=false: every double operation is one correctly rounded
+// IEEE operation in the order the CPU oracle performs it, so trajectories,
+// counters and times match the oracle bit for bit.
+#include "lane_kernel.cuh"
 
 namespace tl {
 namespace {
 
-constexpr int kStride = 33;
-constexpr int kBatch = 4;
-constexpr int kNodes = 63;
-enum : int { P_NEED = 0, P_TOP = 1, P_SSA = 2, P_DONE = 3, P_IDLE = 4 };
-
-__host__ __device__ constexpr int node_base(int k) { return 64 - (64 >> k); }
-
-__host__ __device__ inline size_t r16(size_t v) { return (v + 15) & ~size_t(15); }
-
-__host__ __device__ inline size_t lane_warp_bytes(int N, int M)
-{
-    return r16(4 * (size_t)kStride * N) + r16(8 * (size_t)kStride * kNodes) + r16(8 * (size_t)M) +
-           r16(8 * (size_t)M) + r16(8 * (size_t)N) + r16((size_t)M) + r16((size_t)N);
-}
-
-struct LaneSmem {
-    int *X;
-    double *V;
-    double *a;
-    long long *k;
-    long long *xn;
-    unsigned char *crit;
-    unsigned char *irs;
-};
-
-__device__ __forceinline__ LaneSmem carve_lane(unsigned char *p, int N, int M)
-{
-    LaneSmem w;
-    w.X = reinterpret_cast<int *>(p);
-    p += r16(4 * (size_t)kStride * N);
-    w.V = reinterpret_cast<double *>(p);
-    p += r16(8 * (size_t)kStride * kNodes);
-    w.a = reinterpret_cast<double *>(p);
-    p += r16(8 * (size_t)M);
-    w.k = reinterpret_cast<long long *>(p);
-    p += r16(8 * (size_t)M);
-    w.xn = reinterpret_cast<long long *>(p);
-    p += r16(8 * (size_t)N);
-    w.crit = p;
-    p += r16((size_t)M);
-    w.irs = p;
-    return w;
-}
-
-constexpr double kDblMax = 1.7976931348623157e308;
-
-__global__ void __launch_bounds__(256) lane_f64_kernel(const SimArgs A)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    int *blob = reinterpret_cast<int *>(smem);
-    for (int i = threadIdx.x; i < A.L.words; i += blockDim.x) blob[i] = A.blob[i];
-    const size_t model_bytes = model_smem_bytes(A.L);
-    double *inv = reinterpret_cast<double *>(smem + model_bytes);
-    for (int k = threadIdx.x; k <= f64::kInversionCap; k += blockDim.x) inv[k] = k ? 1.0 / (double)k : 0.0;
-    __syncthreads();
-    const size_t inv_bytes = r16((f64::kInversionCap + 1) * 8);
-    const int N = A.L.N, M = A.L.M, S = A.S;
-    const LaneSmem w = carve_lane(smem + model_bytes + inv_bytes + (size_t)warp * lane_warp_bytes(N, M), N, M);
-    int *const X = w.X;
-    double *const V = w.V;
-    const int *rinfo = blob + A.L.off_rinfo;
-    const int *nu_ptr = blob + A.L.off_nu_ptr;
-    const int *nu_ent = blob + A.L.off_nu_ent;
-    const int *tr_ptr = blob + A.L.off_tr_ptr;
-    const int *tr_ent = blob + A.L.off_tr_ent;
-    const int *hor = blob + A.L.off_hor;
-    const int *dep_ptr = blob + A.L.off_dep_ptr;
-    const int *dep_ent = blob + A.L.off_dep_ent;
-    const double *T = A.T;
-    const double t_end = A.t_end;
-    const bool exact = (A.mode == SSA_MODE_EXACT);
-    const double kInf = __longlong_as_double(0x7FF0000000000000ll);
-
-    // this lane's simulation
-    long long row = -1;
-    uint32_t sim = 0;
-    double t = 0.0;
-    int ks = 0;
-    uint32_t attempt = 0;
-    int status = SSA_STATUS_OK;
-    int phase = P_NEED;
-    int ssa_left = 0;
-    int first = 0;
-    long long leaps = 0, rejected = 0, ssa_steps = 0, firings = 0;
-    // batched SSA draws: -ln u1 and u2 for attempts eb_att .. eb_att + kBatch - 1
-    bool eb_valid = false;
-    uint32_t eb_att = 0;
-    double eb_E[kBatch], eb_U[kBatch];
-
-    auto own_prop = [&](int j) -> double {
-        return propensity_col(rinfo[j], __ldg(A.params + (size_t)row * M + j), X, kStride, lane);
-    };
-    auto lane_record = [&](int k) {
-        int *dst = A.samples + ((size_t)row * S + k) * (size_t)N;
-        for (int i = 0; i < N; ++i) dst[i] = X[i * kStride + lane];
-    };
-    auto lane_build_tree = [&]() {
-        for (int l = 0; l < 32; ++l) {
-            double s = 0.0;
-            for (int j = l; j < M; j += 32) s = s + own_prop(j);
-            V[l * kStride + lane] = s;
-        }
-        for (int k = 1; k <= 5; ++k) {
-            const int width = 32 >> k;
-            for (int c = 0; c < width; ++c)
-                V[(node_base(k) + c) * kStride + lane] =
-                    V[(node_base(k - 1) + c) * kStride + lane] + V[(node_base(k - 1) + c + width) * kStride + lane];
-        }
-    };
-
-    for (;;) {
-        // ---- hand out simulation indices to lanes that need one
-        const unsigned need = __ballot_sync(kFull, phase == P_NEED);
-        if (need) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(A.work_counter, (unsigned long long)__popc(need));
-            base = __shfl_sync(kFull, base, 0);
-            if (phase == P_NEED) {
-                const unsigned long long r = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                if (r < (unsigned long long)A.n_sims) {
-                    row = (long long)r;
-                    sim = (uint32_t)(A.sim_offset + row);
-                    t = 0.0;
-                    ks = 0;
-                    attempt = 0;
-                    status = SSA_STATUS_OK;
-                    leaps = rejected = ssa_steps = firings = 0;
-                    eb_valid = false;
-                    for (int i = 0; i < N; ++i) X[i * kStride + lane] = A.x0[(size_t)row * N + i];
-                    if (exact) lane_build_tree();
-                    phase = P_TOP;
-                } else {
-                    row = -1;
-                    phase = P_IDLE;
-                }
-            }
-        }
-        if (__all_sync(kFull, phase == P_IDLE)) break;
-        __syncwarp();
-
-        // ---- cooperative top of the loop, one simulation at a time
-        if (!exact) {
-            unsigned todo = __ballot_sync(kFull, phase == P_TOP);
-            while (todo) {
-                const int L = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const long long rL = __shfl_sync(kFull, row, L);
-                const uint32_t sL = __shfl_sync(kFull, sim, L);
-                double tL = __shfl_sync(kFull, t, L);
-                int ksL = __shfl_sync(kFull, ks, L);
-                uint32_t attL = __shfl_sync(kFull, attempt, L);
-                long long lpL = __shfl_sync(kFull, leaps, L);
-                long long rjL = __shfl_sync(kFull, rejected, L);
-                const long long fi0 = __shfl_sync(kFull, firings, L);
-                long long fiL = fi0;
-                int stL = SSA_STATUS_OK;
-                int nphase = P_TOP, nleft = 0, nfirst = 0;
-                int *rowout = A.samples + (size_t)rL * S * (size_t)N;
-                const double *cL = A.params + (size_t)rL * M;
-
-                while (ksL < S && T[ksL] <= tL) {
-                    for (int i = lane; i < N; i += 32) rowout[(size_t)ksL * N + i] = X[i * kStride + L];
-                    ++ksL;
-                }
-                if (tL >= t_end) {
-                    nphase = P_DONE;
-                } else if ((long long)attL >= A.max_attempts) {
-                    stL = SSA_STATUS_STEP_LIMIT;
-                    nphase = P_DONE;
-                } else {
-                    double s = 0.0;
-                    for (int j = lane; j < M; j += 32) {
-                        const double a = propensity_col(rinfo[j], cL[j], X, kStride, L);
-                        w.a[j] = a;
-                        s = s + a;
-                    }
-                    double Lv[6];
-                    const double a0 = slot_tree(s, Lv);
-#pragma unroll
-                    for (int k = 0; k <= 5; ++k)
-                        if (lane < (32 >> k)) V[(node_base(k) + lane) * kStride + L] = Lv[k];
-                    __syncwarp();
-                    if (a0 == 0.0) {
-                        tL = t_end;
-                        nphase = P_DONE;
-                    } else if (!(a0 <= kDblMax)) {
-                        stL = SSA_STATUS_INVALID;
-                        nphase = P_DONE;
-                    } else {
-                        // critical set (CGP 2005) and a0c
-                        double sc = 0.0;
-                        for (int j = lane; j < M; j += 32) {
-                            long long Lj = LLONG_MAX;
-                            for (int e = nu_ptr[j]; e < nu_ptr[j + 1]; ++e) {
-                                const int ent = nu_ent[e];
-                                const int nv = (signed char)(ent & 0xff);
-                                if (nv < 0) {
-                                    const long long q = (long long)X[(ent >> 8) * kStride + L] / (long long)(-nv);
-                                    Lj = q < Lj ? q : Lj;
-                                }
-                            }
-                            const double a = w.a[j];
-                            const bool cr = (a > 0.0) && (Lj < (long long)A.n_c);
-                            w.crit[j] = cr;
-                            sc = sc + (cr ? a : 0.0);
-                        }
-                        for (int i = lane; i < N; i += 32) w.irs[i] = 0;
-                        __syncwarp();
-                        double Lc[6];
-                        const double a0c = slot_tree(sc, Lc);
-                        for (int j = lane; j < M; j += 32) {
-                            if (w.crit[j]) continue;
-                            const int info = rinfo[j];
-                            const int kind = info & 3;
-                            if (kind >= 1) w.irs[(info >> 2) & 0x7fff] = 1;
-                            if (kind == 2) w.irs[(info >> 17) & 0x7fff] = 1;
-                        }
-                        __syncwarp();
-                        // tau' (CGP 2006) over the reactant species of noncritical reactions
-                        unsigned long long tmin = 0x7FF0000000000000ull;
-                        for (int i = lane; i < N; i += 32) {
-                            if (!w.irs[i]) continue;
-                            double mu = 0.0, sig2 = 0.0;
-                            for (int e = tr_ptr[i]; e < tr_ptr[i + 1]; ++e) {
-                                const int ent = tr_ent[e];
-                                const int j = ent >> 8;
-                                if (w.crit[j]) continue;
-                                const double a = w.a[j];
-                                if (!(a > 0.0)) continue;
-                                const int nv = (signed char)(ent & 0xff);
-                                mu = mu + (double)nv * a;
-                                sig2 = sig2 + (double)(nv * nv) * a;
-                            }
-                            const int xi = X[i * kStride + L];
-                            const double xd = (double)xi;
-                            double g;
-                            const int h = hor[i];
-                            if (h == 1) g = 1.0;
-                            else if (h == 2) g = 2.0;
-                            else g = (xi >= 2) ? 2.0 + 1.0 / (xd - 1.0) : 2.0;
-                            double bound = (A.eps * xd) / g;
-                            if (bound < 1.0) bound = 1.0;
-                            if (mu != 0.0) {
-                                const unsigned long long b1 =
-                                    (unsigned long long)__double_as_longlong(bound / fabs(mu));
-                                tmin = b1 < tmin ? b1 : tmin;
-                            }
-                            if (sig2 != 0.0) {
-                                const unsigned long long b2 =
-                                    (unsigned long long)__double_as_longlong((bound * bound) / sig2);
-                                tmin = b2 < tmin ? b2 : tmin;
-                            }
-                        }
-                        double tau1 = __longlong_as_double((long long)warp_min_u64(tmin));
-
-                        int halvings = 0;
-                        for (;;) {
-                            if (tau1 < A.ssa_factor / a0) {
-                                nphase = P_SSA;
-                                nleft = A.ssa_block;
-                                nfirst = 1;
-                                break;
-                            }
-                            if ((long long)attL >= A.max_attempts) {
-                                stL = SSA_STATUS_STEP_LIMIT;
-                                nphase = P_DONE;
-                                break;
-                            }
-                            attL = attL + 1;
-                            const uint4 wl = f64::draw(A.seed, sL, attL, PURPOSE_LEAP, 0, 0);
-                            const double u_tau = f64::u01(wl.x, wl.y);
-                            const double u_sel = f64::u01(wl.z, wl.w);
-                            const double tau2 = (a0c > 0.0) ? -f64::dlog(u_tau) / a0c : kInf;
-                            const double t_stop = (ksL < S) ? T[ksL] : t_end;
-                            const double delta = t_stop - tL;
-                            double tau;
-                            int jc = -1;
-                            bool clamp = false;
-                            if (tau2 <= tau1 && tau2 <= delta) {
-                                tau = tau2;
-                                jc = slot_select(Lc, u_sel * a0c, w.a, w.crit, true, M);
-                            } else if (delta <= tau1) {
-                                tau = delta;
-                                clamp = true;
-                            } else {
-                                tau = tau1;
-                            }
-                            int krej = 0, kover = 0;
-                            long long ksum = 0;
-                            for (int j = lane; j < M; j += 32) {
-                                long long kj;
-                                if (w.crit[j]) {
-                                    kj = (j == jc) ? 1 : 0;
-                                } else {
-                                    kj = f64::poisson(w.a[j] * tau, A.seed, sL, attL, (uint32_t)j, inv);
-                                    if (kj < 0) krej = 1;
-                                    else if (kj > f64::kCountLimit) kover = 1;
-                                }
-                                w.k[j] = kj;
-                                ksum += kj;
-                            }
-                            if (__any_sync(kFull, krej)) {
-                                stL = SSA_STATUS_REJECT_LIMIT;
-                                nphase = P_DONE;
-                                break;
-                            }
-                            if (__any_sync(kFull, kover)) {
-                                stL = SSA_STATUS_OVERFLOW;
-                                nphase = P_DONE;
-                                break;
-                            }
-                            __syncwarp();
-                            int neg = 0, big = 0;
-                            for (int i = lane; i < N; i += 32) {
-                                long long xn = X[i * kStride + L];
-                                for (int e = tr_ptr[i]; e < tr_ptr[i + 1]; ++e) {
-                                    const int ent = tr_ent[e];
-                                    xn += w.k[ent >> 8] * (long long)(signed char)(ent & 0xff);
-                                }
-                                w.xn[i] = xn;
-                                neg |= (xn < 0);
-                                big |= (xn > INT_MAX);
-                            }
-                            if (__any_sync(kFull, neg)) {
-                                rjL += 1;
-                                halvings += 1;
-                                if (halvings > A.max_halvings) {
-                                    stL = SSA_STATUS_REJECT_LIMIT;
-                                    nphase = P_DONE;
-                                    break;
-                                }
-                                tau1 = tau1 / 2.0;
-                                continue;
-                            }
-                            if (__any_sync(kFull, big)) {
-                                stL = SSA_STATUS_OVERFLOW;
-                                nphase = P_DONE;
-                                break;
-                            }
-                            for (int i = lane; i < N; i += 32) X[i * kStride + L] = (int)w.xn[i];
-                            fiL += warp_sum_i64(ksum);
-                            tL = clamp ? t_stop : tL + tau;
-                            lpL += 1;
-                            break;
-                        }
-                    }
-                }
-                __syncwarp();
-                if (lane == L) {
-                    t = tL;
-                    ks = ksL;
-                    attempt = attL;
-                    status = stL;
-                    leaps = lpL;
-                    rejected = rjL;
-                    firings = fiL;
-                    phase = nphase;
-                    ssa_left = nleft;
-                    first = nfirst;
-                }
-            }
-            __syncwarp();
-        }
-
-        // ---- lane-local part: exact-mode top of the loop
-        if (exact && phase == P_TOP) {
-            while (ks < S && T[ks] <= t) lane_record(ks++);
-            if (t >= t_end) {
-                phase = P_DONE;
-            } else if ((long long)attempt >= A.max_attempts) {
-                status = SSA_STATUS_STEP_LIMIT;
-                phase = P_DONE;
-            } else {
-                const double a0 = V[62 * kStride + lane];
-                if (a0 == 0.0) {
-                    t = t_end;
-                    phase = P_DONE;
-                } else if (!(a0 <= kDblMax)) {
-                    status = SSA_STATUS_INVALID;
-                    phase = P_DONE;
-                } else {
-                    phase = P_SSA;
-                    ssa_left = 1;
-                    first = 1;
-                }
-            }
-        }
-
-        // ---- lane-local part: one exact SSA step (direct method)
-        if (phase == P_SSA) {
-            if (!first && !f64::nn_gt(t_end, t)) {
-                phase = P_TOP;
-            } else {
-                const double a0 = V[62 * kStride + lane];
-                if (f64::dbits(a0) == 0) {
-                    t = t_end;
-                    phase = P_DONE;
-                } else if (f64::dbits(a0) > 0x7FEFFFFFFFFFFFFFll) {
-                    status = SSA_STATUS_INVALID;
-                    phase = P_DONE;
-                } else if ((long long)attempt >= A.max_attempts) {
-                    status = SSA_STATUS_STEP_LIMIT;
-                    phase = P_DONE;
-                } else {
-                    attempt = attempt + 1;
-                    // -ln u1 and u2 of this attempt; the next kBatch attempts are drawn
-                    // together so their log chains overlap (same values as one by one)
-                    if (!(eb_valid && attempt - eb_att < (uint32_t)kBatch)) {
-                        eb_att = attempt;
-                        eb_valid = true;
-#pragma unroll
-                        for (int q = 0; q < kBatch; ++q) {
-                            const uint4 wb = f64::draw(A.seed, sim, attempt + q, PURPOSE_SSA, 0, 0);
-                            eb_E[q] = -f64::dlog(f64::u01(wb.x, wb.y));
-                            eb_U[q] = f64::u01(wb.z, wb.w);
-                        }
-                    }
-                    const uint32_t pos = attempt - eb_att;
-                    double E = eb_E[0], u2 = eb_U[0];
-#pragma unroll
-                    for (int q = 1; q < kBatch; ++q)
-                        if (pos == (uint32_t)q) {
-                            E = eb_E[q];
-                            u2 = eb_U[q];
-                        }
-                    const double tau = E / a0;
-                    const double t_new = t + tau;
-                    while (ks < S && !f64::nn_ge(T[ks], t_new)) lane_record(ks++);
-                    if (f64::nn_gt(t_new, t_end)) {
-                        t = t_end;
-                        phase = P_DONE;
-                    } else {
-                        // descend the slot tree, then walk the chosen slot
-                        double target = u2 * a0;
-                        int cls = 0;
-#pragma unroll
-                        for (int k = 4; k >= 0; --k) {
-                            const int step = 1 << (4 - k);
-                            const double left = V[(node_base(k) + cls) * kStride + lane];
-                            const double right = V[(node_base(k) + cls + step) * kStride + lane];
-                            if (f64::nn_ge(target, left) && f64::nn_pos(right)) {
-                                target = target - left;
-                                cls += step;
-                            }
-                        }
-                        double cum = 0.0;
-                        int jf = -1, last = -1;
-                        for (int j = cls; j < M; j += 32) {
-                            const double v = own_prop(j);
-                            cum = cum + v;
-                            if (f64::nn_pos(v)) last = j;
-                            if (f64::nn_gt(cum, target)) {
-                                jf = j;
-                                break;
-                            }
-                        }
-                        if (jf < 0) jf = last;
-                        if (jf < 0) {
-                            status = SSA_STATUS_INVALID;
-                            phase = P_DONE;
-                        } else {
-                            const int e0 = nu_ptr[jf], e1 = nu_ptr[jf + 1];
-                            bool over = false;
-                            for (int e = e0; e < e1; ++e) {
-                                const int ent = nu_ent[e];
-                                if ((long long)X[(ent >> 8) * kStride + lane] + (signed char)(ent & 0xff) > INT_MAX)
-                                    over = true;
-                            }
-                            if (over) {
-                                status = SSA_STATUS_OVERFLOW;
-                                phase = P_DONE;
-                            } else {
-                                unsigned dirty = 0;
-                                for (int e = e0; e < e1; ++e) {
-                                    const int ent = nu_ent[e];
-                                    const int sp = ent >> 8;
-                                    X[sp * kStride + lane] += (signed char)(ent & 0xff);
-                                    for (int d = dep_ptr[sp]; d < dep_ptr[sp + 1]; ++d) dirty |= 1u << (dep_ent[d] & 31);
-                                }
-                                unsigned m = dirty;
-                                while (m) {
-                                    const int l = __ffs(m) - 1;
-                                    m &= m - 1;
-                                    double s = 0.0;
-                                    for (int j = l; j < M; j += 32) s = s + own_prop(j);
-                                    V[l * kStride + lane] = s;
-                                }
-#pragma unroll
-                                for (int k = 1; k <= 5; ++k) {
-                                    const int width = 32 >> k;
-                                    dirty = (dirty | (dirty >> width)) & ((1u << width) - 1u);
-                                    unsigned q = dirty;
-                                    while (q) {
-                                        const int c = __ffs(q) - 1;
-                                        q &= q - 1;
-                                        V[(node_base(k) + c) * kStride + lane] =
-                                            V[(node_base(k - 1) + c) * kStride + lane] +
-                                            V[(node_base(k - 1) + c + width) * kStride + lane];
-                                    }
-                                }
-                                t = t_new;
-                                ssa_steps += 1;
-                                firings += 1;
-                                first = 0;
-                                if (--ssa_left == 0) phase = P_TOP;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-
-        // ---- finished simulations: remaining samples hold the final state
-        if (phase == P_DONE) {
-            while (ks < S) lane_record(ks++);
-            if (A.stats != nullptr) {
-                ssa_sim_stats st;
-                st.status = status;
-                st.reserved = 0;
-                st.leaps = leaps;
-                st.rejected = rejected;
-                st.ssa_steps = ssa_steps;
-                st.firings = firings;
-                st.attempts = attempt;
-                st.t_final = t;
-                A.stats[row] = st;
-            }
-            phase = P_NEED;
-        }
-        __syncwarp();
+struct RefArith {
+    __device__ static __forceinline__ double prop(int info, double c, const int *X, int stride, int col)
+    {
+        return propensity_col(info, c, X, stride, col);
     }
-}
+    __device__ static __forceinline__ void uniforms(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t purpose,
+                                                    double &ua, double &ub)
+    {
+        const uint4 w = f64::draw(seed, sim, attempt, purpose, 0, 0);
+        ua = f64::u01(w.x, w.y);
+        ub = f64::u01(w.z, w.w);
+    }
+    __device__ static __forceinline__ double neglog(double u) { return -f64::dlog(u); }
+    __device__ static __forceinline__ double tau_of(double E, double a) { return E / a; }
+    __device__ static __forceinline__ long long poisson(double a, double tau, uint64_t seed, uint32_t sim,
+                                                        uint32_t attempt, uint32_t j, const double *inv)
+    {
+        return f64::poisson(a * tau, seed, sim, attempt, j, inv);
+    }
+};
 
 }  // namespace
 
-size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps)
-{
-    return model_smem_bytes(L) + r16((f64::kInversionCap + 1) * 8) + (size_t)block_warps * lane_warp_bytes(L.N, L.M);
-}
+size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps) { return lane_smem_bytes(L, block_warps); }
 
 cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(lane_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    lane_f64_kernel<<<grid, block_warps * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_lane_impl<RefArith>(a, block_warps, grid, smem, s);
 }
 
-int lane_ref_occupancy(int block_warps, size_t smem)
-{
-    int nb = 0;
-    if (cudaFuncSetAttribute(lane_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lane_f64_kernel, block_warps * 32, smem) != cudaSuccess)
-        return 0;
-    return nb;
-}
+int lane_ref_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<RefArith>(block_warps, smem); }
 
 }  // namespace tl

@@ -1,0 +1,59 @@
+// Fast-mode instantiation of the lane-per-simulation kernel.
+//
+// FP32: propensities a_j, Poisson means a_j tau and the Poisson sampler,
+// -ln u and the event times E/a.  FP64: the simulated clock, the slot tree
+// (a0 and a0c as FP64 sums of the FP32 propensities), the critical test and
+// tau' (mu_i, sigma_i^2, the bounds and their minimum), as the reference
+// mode.  Counts stay exact integers.  Random numbers come from the same
+// Philox words as the reference mode, so the two modes are coupled.
+#include "device_fast.cuh"
+#include "lane_kernel.cuh"
+
+namespace tl {
+namespace {
+
+struct FastArith {
+    __device__ static __forceinline__ double prop(int info, double c, const int *X, int stride, int col)
+    {
+        const int kind = info & 3;
+        const int s0 = (info >> 2) & 0x7fff;
+        const int s1 = (info >> 17) & 0x7fff;
+        const float cf = (float)c;
+        if (kind == 0) return (double)cf;
+        if (kind == 1) return (double)(cf * (float)X[s0 * stride + col]);
+        if (kind == 2) return (double)((cf * (float)X[s0 * stride + col]) * (float)X[s1 * stride + col]);
+        const long long xi = X[s0 * stride + col];
+        return (double)(cf * (float)((xi * (xi - 1)) / 2));
+    }
+    __device__ static __forceinline__ void uniforms(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t purpose,
+                                                    double &ua, double &ub)
+    {
+        // the reference mode's 53-bit uniforms: -ln u is then taken in FP32,
+        // while selection targets u * a0 keep the full resolution
+        const uint4 w = f64::draw(seed, sim, attempt, purpose, 0, 0);
+        ua = f64::u01(w.x, w.y);
+        ub = f64::u01(w.z, w.w);
+    }
+    __device__ static __forceinline__ double neglog(double u)
+    {
+        // u in (0,1) rounded to FP32 stays in (0,1]; -ln 1 = 0 is a zero-length step
+        return (double)(-logf((float)u));
+    }
+    __device__ static __forceinline__ double tau_of(double E, double a) { return (double)((float)E / (float)a); }
+    __device__ static __forceinline__ long long poisson(double a, double tau, uint64_t seed, uint32_t sim,
+                                                        uint32_t attempt, uint32_t j, const double *)
+    {
+        return fast::poisson((float)a * (float)tau, seed, sim, attempt, j);
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
+{
+    return launch_lane_impl<FastArith>(a, block_warps, grid, smem, s);
+}
+
+int lane_fast_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<FastArith>(block_warps, smem); }
+
+}  // namespace tl
