@@ -107,7 +107,7 @@ typedef struct {
     int32_t layout;       /* SSA_LAYOUT_* (AUTO) */
     int64_t max_attempts; /* per-simulation cap on leap attempts + SSA steps (1e8) */
     int32_t block_warps;  /* warps per CTA, 0 = automatic */
-    int32_t reserved;
+    int32_t sims_per_warp; /* lane layout: lanes of a warp that own a simulation (1..32, 0 = 32) */
 } ssa_options;
 
 /* Per-simulation counters and status (56 bytes). */

@@ -66,7 +66,7 @@ class Options(ctypes.Structure):
         ("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("eps", ctypes.c_double),
         ("n_c", ctypes.c_int32), ("ssa_block", ctypes.c_int32), ("ssa_factor", ctypes.c_double),
         ("max_halvings", ctypes.c_int32), ("layout", ctypes.c_int32), ("max_attempts", ctypes.c_int64),
-        ("block_warps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("block_warps", ctypes.c_int32), ("sims_per_warp", ctypes.c_int32),
     ]
 
 

@@ -258,6 +258,7 @@ static int check_options(const ssa_options *o)
     if (o->layout != SSA_LAYOUT_AUTO && o->layout != SSA_LAYOUT_WARP && o->layout != SSA_LAYOUT_LANE)
         return fail(SSA_EUNSUPPORTED, "unknown layout");
     if (o->block_warps < 0 || o->block_warps > 8) return fail(SSA_EINVAL, "block_warps must be in 0..8");
+    if (o->sims_per_warp < 0 || o->sims_per_warp > 32) return fail(SSA_EINVAL, "sims_per_warp must be in 0..32");
     return SSA_OK;
 }
 
@@ -307,7 +308,8 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
                         ? (fast ? tl::lane_fast_occupancy(warps, smem) : tl::lane_ref_occupancy(warps, smem))
                         : tl::warp_ref_occupancy(warps, smem);
     const int per_sm = std::max(1, occ);
-    const long long sims_per_block = (long long)warps * (layout == SSA_LAYOUT_LANE ? 32 : 1);
+    const int spw = o.sims_per_warp > 0 ? o.sims_per_warp : 32;
+    const long long sims_per_block = (long long)warps * (layout == SSA_LAYOUT_LANE ? spw : 1);
     const long long need_blocks = (n_sims + sims_per_block - 1) / sims_per_block;
     const int grid = (int)std::min<long long>((long long)per_sm * sms, need_blocks);
 
@@ -329,6 +331,7 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     a.ssa_block = o.ssa_block;
     a.max_halvings = o.max_halvings;
     a.max_attempts = o.max_attempts;
+    a.sims_per_warp = spw;
     a.samples = samples;
     a.stats = stats;
     void *counter = counter_in;

@@ -212,11 +212,13 @@ __device__ __forceinline__ long long poisson(double lam, uint64_t seed, uint32_t
         return k;
     }
     const double slam = sqrt(lam);
-    const double loglam = dlog(lam);
     const double b = 0.931 + 2.53 * slam;
     const double a = -0.059 + 0.02483 * b;
-    const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
     const double vr = 0.9277 - 3.6224 / (b - 2.0);
+    // ln lam and 1/alpha serve only the acceptance test after the squeeze,
+    // so they are formed on first use (same values, shorter common path)
+    double loglam = 0.0, inv_alpha = 0.0;
+    bool slow_ready = false;
     for (uint32_t it = 0; it < (uint32_t)kPtrsMaxIters; ++it) {
         const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
         const double U = u01(w.x, w.y) - 0.5;
@@ -226,6 +228,11 @@ __device__ __forceinline__ long long poisson(double lam, uint64_t seed, uint32_t
         if (us >= 0.07 && V <= vr) return (kd > (double)kCountLimit) ? kCountLimit + 1 : (long long)kd;
         if (kd < 0.0 || (us < 0.013 && V > us)) continue;
         if (kd > (double)kCountLimit) return kCountLimit + 1;
+        if (!slow_ready) {
+            loglam = dlog(lam);
+            inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+            slow_ready = true;
+        }
         const double lhs = dlog(V * inv_alpha / (a / (us * us) + b));
         const double rhs = -lam + kd * loglam - dlnfact((long long)kd);
         if (lhs <= rhs) return (long long)kd;

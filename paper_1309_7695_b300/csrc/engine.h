@@ -47,6 +47,7 @@ struct SimArgs {
     int32_t ssa_block;
     int32_t max_halvings;
     int64_t max_attempts;
+    int32_t sims_per_warp;
     int32_t *samples;
     ssa_sim_stats *stats;
     unsigned long long *work_counter;

@@ -347,7 +347,7 @@ finished:
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(256) warp_f64_kernel(const SimArgs A)
+__global__ void __launch_bounds__(256, 1) warp_f64_kernel(const SimArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;

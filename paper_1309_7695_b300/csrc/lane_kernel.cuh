@@ -97,7 +97,7 @@ __device__ __forceinline__ LaneSmem carve_lane(unsigned char *p, int N, int M)
 constexpr double kDblMax = 1.7976931348623157e308;
 
 template <class Arith>
-__global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
+__global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
     int ssa_left = 0;
     int first = 0;
     long long leaps = 0, rejected = 0, ssa_steps = 0, firings = 0;
+    double tnext = kInf;   // T[ks], or +inf once every sample is recorded
     // batched SSA draws: -ln u1 and u2 for attempts eb_att .. eb_att + kBatch - 1
     bool eb_valid = false;
     uint32_t eb_att = 0;
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
 
     for (;;) {
         // ---- hand out simulation indices to lanes that need one
+        if (phase == P_NEED && lane >= A.sims_per_warp) phase = P_IDLE;   // lanes without a simulation slot
         const unsigned need = __ballot_sync(kFull, phase == P_NEED);
         if (need) {
             unsigned long long base = 0;
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
                     status = SSA_STATUS_OK;
                     leaps = rejected = ssa_steps = firings = 0;
                     eb_valid = false;
+                    tnext = (S > 0) ? T[0] : kInf;
                     for (int i = 0; i < N; ++i) X[i * kStride + lane] = A.x0[(size_t)row * N + i];
                     if (exact) lane_build_tree();
                     phase = P_TOP;
@@ -213,9 +216,11 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
                 int *rowout = A.samples + (size_t)rL * S * (size_t)N;
                 const double *cL = A.params + (size_t)rL * M;
 
-                while (ksL < S && T[ksL] <= tL) {
+                double tnL = __shfl_sync(kFull, tnext, L);
+                while (ksL < S && tnL <= tL) {
                     for (int i = lane; i < N; i += 32) rowout[(size_t)ksL * N + i] = X[i * kStride + L];
                     ++ksL;
+                    tnL = (ksL < S) ? T[ksL] : kInf;
                 }
                 if (tL >= t_end) {
                     nphase = P_DONE;
@@ -250,7 +255,9 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
                                 const int ent = nu_ent[e];
                                 const int nv = (signed char)(ent & 0xff);
                                 if (nv < 0) {
-                                    const long long q = (long long)X[(ent >> 8) * kStride + L] / (long long)(-nv);
+                                    // a consumed species has |nu| <= 2 (reactant coefficients <= 2)
+                                    const int xq = X[(ent >> 8) * kStride + L];
+                                    const long long q = (nv == -1) ? xq : (xq >> 1);
                                     Lj = q < Lj ? q : Lj;
                                 }
                             }
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
                             double u_tau, u_sel;
                             Arith::uniforms(A.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
                             const double tau2 = (a0c > 0.0) ? Arith::tau_of(Arith::neglog(u_tau), a0c) : kInf;
-                            const double t_stop = (ksL < S) ? T[ksL] : t_end;
+                            const double t_stop = (ksL < S) ? tnL : t_end;
                             const double delta = t_stop - tL;
                             double tau;
                             int jc = -1;
@@ -403,6 +410,7 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
                 if (lane == L) {
                     t = tL;
                     ks = ksL;
+                    tnext = tnL;
                     attempt = attL;
                     status = stL;
                     leaps = lpL;
@@ -418,7 +426,10 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
 
         // ---- lane-local part: exact-mode top of the loop
         if (exact && phase == P_TOP) {
-            while (ks < S && T[ks] <= t) lane_record(ks++);
+            while (ks < S && tnext <= t) {
+                lane_record(ks++);
+                tnext = (ks < S) ? T[ks] : kInf;
+            }
             if (t >= t_end) {
                 phase = P_DONE;
             } else if ((long long)attempt >= A.max_attempts) {
@@ -479,7 +490,10 @@ __global__ void __launch_bounds__(256) lane_kernel(const SimArgs A)
                         }
                     const double tau = Arith::tau_of(E, a0);
                     const double t_new = t + tau;
-                    while (ks < S && !f64::nn_ge(T[ks], t_new)) lane_record(ks++);
+                    while (ks < S && !f64::nn_ge(tnext, t_new)) {
+                        lane_record(ks++);
+                        tnext = (ks < S) ? T[ks] : kInf;
+                    }
                     if (f64::nn_gt(t_new, t_end)) {
                         t = t_end;
                         phase = P_DONE;

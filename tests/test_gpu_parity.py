@@ -150,12 +150,13 @@ def test_degenerate_sizes(layout):
     assert_same(gpu_run(one, layout=layout), oracle_run(one), "n=1")
 
 
-@pytest.mark.parametrize("block_warps", [1, 2, 4, 8])
-def test_launch_shape_does_not_change_results(block_warps):
+@pytest.mark.parametrize("block_warps,sims_per_warp", [(1, 0), (2, 0), (4, 0), (8, 0), (4, 1), (2, 7), (1, 16)])
+def test_launch_shape_does_not_change_results(block_warps, sims_per_warp):
     b = inputs.random_batch(32, 64, 300, seed=12, t_end=20.0, n_samples=11)
     ref = gpu_run(b, seed=3, max_attempts=100_000, layout=abi.SSA_LAYOUT_WARP)
-    got = gpu_run(b, seed=3, max_attempts=100_000, layout=abi.SSA_LAYOUT_LANE, block_warps=block_warps)
-    assert_same(got, ref, f"block_warps={block_warps}")
+    got = gpu_run(b, seed=3, max_attempts=100_000, layout=abi.SSA_LAYOUT_LANE, block_warps=block_warps,
+                  sims_per_warp=sims_per_warp)
+    assert_same(got, ref, f"block_warps={block_warps} sims_per_warp={sims_per_warp}")
 
 
 def test_sharding_by_sim_offset_is_bit_identical():
