@@ -171,6 +171,35 @@ int ssa_simulate_dev_noalloc(ssa_model_t model, int64_t n_sims, int64_t sim_offs
                              const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
                              void *stream);
 
+/* One group of a multi-network launch: a loaded network and its batch.
+ * Array members are DEVICE pointers with the layouts of ssa_simulate_dev;
+ * all models must live on the same device. */
+typedef struct {
+    ssa_model_t model;
+    int64_t n_sims;
+    int64_t sim_offset;           /* global index of the group's first simulation (RNG identity) */
+    const double *params;         /* [n_sims][M] */
+    const int32_t *x0;            /* [n_sims][N] */
+    double t_end;
+    const double *sample_times;   /* [n_samples] */
+    int32_t n_samples;
+    int32_t reserved;
+    uint64_t seed;
+    int32_t *samples;             /* [n_sims][n_samples][N] output */
+    ssa_sim_stats *stats;         /* [n_sims] output, may be NULL */
+} ssa_group;
+
+/* Heterogeneous batch in ONE persistent launch: lanes take simulations from
+ * all groups through a single work counter, in the order the groups are
+ * given (put the most expensive groups first to shorten the tail), each
+ * lane running its own group's network, read from global memory.  The
+ * per-warp workspace is sized for the largest network.  Results per
+ * simulation are identical to ssa_simulate_dev of its group with the same
+ * options and seed.  opts->precision applies to every group; the lane
+ * layout is used.  Allocates (stream-ordered) the group table and the work
+ * counter and frees them on `stream`. */
+int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_options *opts, void *stream);
+
 /* Host-buffer form.  Copies the HOST inputs to device memory that the job
  * owns and enqueues the simulation on `stream` (NULL = a stream the job
  * creates).  The inputs may be reused once this returns.  Fails with

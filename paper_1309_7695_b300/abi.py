@@ -42,7 +42,7 @@ SSA_LAYOUT_LANE = 2
 
 EXPORTED = [
     "ssa_default_options", "ssa_load_model", "ssa_free_model", "ssa_model_info",
-    "ssa_simulate_dev", "ssa_simulate_dev_noalloc", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
+    "ssa_simulate_dev", "ssa_simulate_dev_noalloc", "ssa_simulate_multi_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
     "ssa_release_job", "ssa_last_error", "ssa_abi_version",
 ]
 
@@ -58,6 +58,15 @@ class ModelDesc(ctypes.Structure):
         ("n_species", ctypes.c_int32), ("n_reactions", ctypes.c_int32),
         ("react_ptr", ctypes.c_void_p), ("react_species", ctypes.c_void_p), ("react_coef", ctypes.c_void_p),
         ("prod_ptr", ctypes.c_void_p), ("prod_species", ctypes.c_void_p), ("prod_coef", ctypes.c_void_p),
+    ]
+
+
+class Group(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_void_p), ("n_sims", ctypes.c_int64), ("sim_offset", ctypes.c_int64),
+        ("params", ctypes.c_void_p), ("x0", ctypes.c_void_p), ("t_end", ctypes.c_double),
+        ("sample_times", ctypes.c_void_p), ("n_samples", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("samples", ctypes.c_void_p), ("stats", ctypes.c_void_p),
     ]
 
 
@@ -96,6 +105,7 @@ def lib():
     L.ssa_model_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.ssa_simulate_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp, vp, vp]
     L.ssa_simulate_dev_noalloc.argtypes = L.ssa_simulate_dev.argtypes
+    L.ssa_simulate_multi_dev.argtypes = [i32, ctypes.POINTER(Group), ctypes.POINTER(Options), vp]
     L.ssa_submit_batch.argtypes = [vp, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp,
                                    ctypes.POINTER(vp)]
     L.ssa_poll.argtypes = [vp, ctypes.POINTER(i32)]
@@ -198,6 +208,27 @@ def ssa_simulate_dev_noalloc(model: Model, params, x0, t_end, sample_times, samp
                                           _ptr(sample_times), int(sample_times.numel()), int(seed),
                                           ctypes.byref(o), _ptr(samples), _ptr(stats),
                                           ctypes.c_void_p(int(handle))))
+
+
+def ssa_simulate_multi_dev(groups, opts=None, stream=None):
+    """One persistent launch over several (model, batch) groups.
+
+    ``groups``: sequence of dicts with keys model (Model), params, x0,
+    sample_times, samples, stats (torch CUDA tensors; stats may be None),
+    t_end, seed and optionally sim_offset, in schedule order."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    arr = (Group * len(groups))()
+    for k, g in enumerate(groups):
+        p = g["params"]
+        arr[k] = Group(g["model"].handle, int(p.shape[0]) if p.dim() == 2 else 0, int(g.get("sim_offset", 0)),
+                       _ptr(p), _ptr(g["x0"]), float(g["t_end"]), _ptr(g["sample_times"]),
+                       int(g["sample_times"].numel()), 0, int(g["seed"]), _ptr(g["samples"]),
+                       _ptr(g.get("stats")))
+    o = opts if opts is not None else ssa_default_options()
+    _check(lib().ssa_simulate_multi_dev(len(groups), arr, ctypes.byref(o), ctypes.c_void_p(int(handle))))
 
 
 class Job:

@@ -557,6 +557,98 @@ int ssa_release_job(ssa_job_t j)
     return SSA_OK;
 }
 
+int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_options *opts, void *stream)
+{
+    g_error.clear();
+    if (n_groups < 0 || (n_groups > 0 && !groups)) return fail(SSA_EINVAL, "bad group list");
+    if (n_groups == 0) return SSA_OK;
+    ssa_options o;
+    if (opts) o = *opts;
+    else ssa_default_options(&o);
+    int rc = check_options(&o);
+    if (rc) return rc;
+    if (o.layout == SSA_LAYOUT_WARP) return fail(SSA_EUNSUPPORTED, "multi-network launches use the lane layout");
+    const int device = groups[0].model ? groups[0].model->device : -1;
+    std::vector<tl::GroupArgs> table((size_t)n_groups);
+    int64_t first = 0;
+    int max_N = 1, max_M = 1;
+    for (int g = 0; g < n_groups; ++g) {
+        const ssa_group &G = groups[g];
+        if (!G.model) return fail(SSA_EINVAL, "group " + std::to_string(g) + ": null model");
+        if (G.model->device != device) return fail(SSA_EINVAL, "all groups must use models on one device");
+        if (G.n_sims < 0 || G.sim_offset < 0 || G.sim_offset + G.n_sims > (1ll << 32))
+            return fail(SSA_EINVAL, "group " + std::to_string(g) + ": n_sims/sim_offset out of range");
+        if (G.n_samples < 0 || !(G.t_end >= 0.0) || !std::isfinite(G.t_end))
+            return fail(SSA_EINVAL, "group " + std::to_string(g) + ": bad t_end or n_samples");
+        if (G.n_sims > 0 && (!G.params || !G.x0 || (G.n_samples > 0 && (!G.sample_times || !G.samples))))
+            return fail(SSA_EINVAL, "group " + std::to_string(g) + ": null device array");
+        tl::GroupArgs &R = table[(size_t)g];
+        R.L = G.model->L;
+        R.blob = G.model->d_blob;
+        R.params = G.params;
+        R.x0 = G.x0;
+        R.T = G.sample_times;
+        R.S = G.n_samples;
+        R.t_end = G.t_end;
+        R.n_sims = G.n_sims;
+        R.sim_offset = G.sim_offset;
+        R.seed = G.seed;
+        R.samples = G.samples;
+        R.stats = G.stats;
+        R.first = first;
+        first += G.n_sims;
+        max_N = std::max(max_N, R.L.N);
+        max_M = std::max(max_M, R.L.M);
+    }
+    if (first == 0) return SSA_OK;
+    DeviceGuard guard(device);
+    if (!guard.ok) return fail(SSA_ECUDA, "cannot select the models' device");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int sms = 0, smem_optin = 0;
+    TL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    TL_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    const bool fast = (o.precision == SSA_FAST);
+    int warps = o.block_warps > 0 ? o.block_warps : 4;
+    while (warps > 1 && tl::lane_multi_smem_bytes(max_N, max_M, warps) > (size_t)smem_optin) --warps;
+    const size_t smem = tl::lane_multi_smem_bytes(max_N, max_M, warps);
+    if (smem > (size_t)smem_optin) return fail(SSA_EUNSUPPORTED, "largest network too large for the workspace");
+    const int occ = fast ? tl::lane_multi_fast_occupancy(warps, smem) : tl::lane_multi_ref_occupancy(warps, smem);
+    const int spw = o.sims_per_warp > 0 ? o.sims_per_warp : 32;
+    const long long per_block = (long long)warps * spw;
+    const int grid = (int)std::min<long long>((long long)std::max(1, occ) * sms, (first + per_block - 1) / per_block);
+
+    tl::SimArgs a{};
+    a.n_groups = n_groups;
+    a.max_N = max_N;
+    a.max_M = max_M;
+    a.total_sims = first;
+    a.mode = o.mode;
+    a.n_c = o.n_c;
+    a.eps = o.eps;
+    a.ssa_factor = o.ssa_factor;
+    a.ssa_block = o.ssa_block;
+    a.max_halvings = o.max_halvings;
+    a.max_attempts = o.max_attempts;
+    a.sims_per_warp = spw;
+    void *d_table = nullptr, *counter = nullptr;
+    const size_t table_bytes = sizeof(tl::GroupArgs) * table.size();
+    TL_CUDA(cudaMallocAsync(&d_table, table_bytes, s));
+    cudaError_t e = cudaMemcpyAsync(d_table, table.data(), table_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&counter, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        a.groups = static_cast<const tl::GroupArgs *>(d_table);
+        a.work_counter = static_cast<unsigned long long *>(counter);
+        e = fast ? tl::launch_lane_multi_fast(a, warps, grid, smem, s) : tl::launch_lane_multi_ref(a, warps, grid, smem, s);
+    }
+    // the table copy is from pageable host memory, so the copy has been staged
+    // before cudaMemcpyAsync returned and `table` may go out of scope
+    if (counter) cudaFreeAsync(counter, s);
+    if (d_table) cudaFreeAsync(d_table, s);
+    if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("multi launch: ") + cudaGetErrorString(e));
+    return SSA_OK;
+}
+
 int ssa_simulate_dev_noalloc(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
                              const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
                              uint64_t seed, const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,

@@ -29,7 +29,32 @@ struct ModelLayout {
 
 enum : uint32_t { PURPOSE_LEAP = 1u, PURPOSE_POISSON = 2u, PURPOSE_SSA = 3u };
 
+// One group of a multi-network launch: its network (packed blob in global
+// memory), its inputs and outputs, and the flattened index of its first
+// simulation.
+struct GroupArgs {
+    ModelLayout L;
+    const int32_t *blob;
+    const double *params;
+    const int32_t *x0;
+    const double *T;
+    int32_t S;
+    double t_end;
+    int64_t n_sims;
+    int64_t sim_offset;
+    uint64_t seed;
+    int32_t *samples;
+    ssa_sim_stats *stats;
+    int64_t first;
+};
+
 struct SimArgs {
+    // multi-network launch: groups[0..n_groups) in schedule order, flattened
+    // over total_sims simulations; n_groups == 0 for a single-network launch
+    const GroupArgs *groups;
+    int32_t n_groups;
+    int32_t max_N, max_M;
+    int64_t total_sims;
     ModelLayout L;
     const int32_t *blob;
     const double *params;
@@ -81,6 +106,13 @@ int lane_ref_occupancy(int block_warps, size_t smem);
 // Fast-mode instantiation (kernel_lane_fast.cu), same shared-memory layout.
 cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
 int lane_fast_occupancy(int block_warps, size_t smem);
+// Multi-network persistent instantiations (model read from global memory;
+// workspace sized for the largest network, no model staged in shared memory).
+size_t lane_multi_smem_bytes(int max_N, int max_M, int block_warps);
+cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+int lane_multi_ref_occupancy(int block_warps, size_t smem);
+cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+int lane_multi_fast_occupancy(int block_warps, size_t smem);
 
 // Warp-per-simulation FP64 reference kernel (kernel_warp_f64.cu).
 size_t warp_f64_smem_bytes(const ModelLayout &L, int block_warps);

@@ -51,9 +51,19 @@ struct FastArith {
 
 cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
 {
-    return launch_lane_impl<FastArith>(a, block_warps, grid, smem, s);
+    return launch_lane_impl<FastArith, false>(a, block_warps, grid, smem, s);
 }
 
-int lane_fast_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<FastArith>(block_warps, smem); }
+int lane_fast_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<FastArith, false>(block_warps, smem); }
+
+cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
+{
+    return launch_lane_impl<FastArith, true>(a, block_warps, grid, smem, s);
+}
+
+int lane_multi_fast_occupancy(int block_warps, size_t smem)
+{
+    return lane_occupancy_impl<FastArith, true>(block_warps, smem);
+}
 
 }  // namespace tl

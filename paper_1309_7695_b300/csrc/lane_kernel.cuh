@@ -96,37 +96,102 @@ __device__ __forceinline__ LaneSmem carve_lane(unsigned char *p, int N, int M)
 
 constexpr double kDblMax = 1.7976931348623157e308;
 
-template <class Arith>
+// Everything one simulation group needs: network arrays and run arguments.
+struct GroupView {
+    const int *rinfo, *nu_ptr, *nu_ent, *tr_ptr, *tr_ent, *hor, *dep_ptr, *dep_ent;
+    int N, M, S;
+    double t_end;
+    const double *params;
+    const int32_t *x0;
+    const double *T;
+    int32_t *samples;
+    ssa_sim_stats *stats;
+    long long sim_offset, n_sims, first;
+    uint64_t seed;
+};
+
+__device__ __forceinline__ void view_model(GroupView &G, const int *blob, const ModelLayout &L)
+{
+    G.rinfo = blob + L.off_rinfo;
+    G.nu_ptr = blob + L.off_nu_ptr;
+    G.nu_ent = blob + L.off_nu_ent;
+    G.tr_ptr = blob + L.off_tr_ptr;
+    G.tr_ent = blob + L.off_tr_ent;
+    G.hor = blob + L.off_hor;
+    G.dep_ptr = blob + L.off_dep_ptr;
+    G.dep_ent = blob + L.off_dep_ent;
+    G.N = L.N;
+    G.M = L.M;
+}
+
+// single-network launch: the model staged in shared memory
+__device__ __forceinline__ GroupView view_single(const SimArgs &A, const int *smem_blob)
+{
+    GroupView G;
+    view_model(G, smem_blob, A.L);
+    G.S = A.S;
+    G.t_end = A.t_end;
+    G.params = A.params;
+    G.x0 = A.x0;
+    G.T = A.T;
+    G.samples = A.samples;
+    G.stats = A.stats;
+    G.sim_offset = A.sim_offset;
+    G.n_sims = A.n_sims;
+    G.first = 0;
+    G.seed = A.seed;
+    return G;
+}
+
+// multi-network launch: group g read from global memory (L1-cached)
+__device__ __forceinline__ GroupView view_group(const GroupArgs *groups, int g)
+{
+    const GroupArgs &R = groups[g];
+    GroupView G;
+    view_model(G, R.blob, R.L);
+    G.S = R.S;
+    G.t_end = R.t_end;
+    G.params = R.params;
+    G.x0 = R.x0;
+    G.T = R.T;
+    G.samples = R.samples;
+    G.stats = R.stats;
+    G.sim_offset = R.sim_offset;
+    G.n_sims = R.n_sims;
+    G.first = R.first;
+    G.seed = R.seed;
+    return G;
+}
+
+template <class Arith, bool kMulti>
 __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     int *blob = reinterpret_cast<int *>(smem);
-    for (int i = threadIdx.x; i < A.L.words; i += blockDim.x) blob[i] = A.blob[i];
-    const size_t model_bytes = model_smem_bytes(A.L);
+    size_t model_bytes = 0;
+    if (!kMulti) {
+        for (int i = threadIdx.x; i < A.L.words; i += blockDim.x) blob[i] = A.blob[i];
+        model_bytes = model_smem_bytes(A.L);
+    }
     double *inv = reinterpret_cast<double *>(smem + model_bytes);
     for (int k = threadIdx.x; k <= f64::kInversionCap; k += blockDim.x) inv[k] = k ? 1.0 / (double)k : 0.0;
     __syncthreads();
     const size_t inv_bytes = r16((f64::kInversionCap + 1) * 8);
-    const int N = A.L.N, M = A.L.M, S = A.S;
-    const LaneSmem w = carve_lane(smem + model_bytes + inv_bytes + (size_t)warp * lane_warp_bytes(N, M), N, M);
+    const int wN = kMulti ? A.max_N : A.L.N, wM = kMulti ? A.max_M : A.L.M;
+    const LaneSmem w = carve_lane(smem + model_bytes + inv_bytes + (size_t)warp * lane_warp_bytes(wN, wM), wN, wM);
     int *const X = w.X;
     double *const V = w.V;
-    const int *rinfo = blob + A.L.off_rinfo;
-    const int *nu_ptr = blob + A.L.off_nu_ptr;
-    const int *nu_ent = blob + A.L.off_nu_ent;
-    const int *tr_ptr = blob + A.L.off_tr_ptr;
-    const int *tr_ent = blob + A.L.off_tr_ent;
-    const int *hor = blob + A.L.off_hor;
-    const int *dep_ptr = blob + A.L.off_dep_ptr;
-    const int *dep_ent = blob + A.L.off_dep_ent;
-    const double *T = A.T;
-    const double t_end = A.t_end;
+    GroupView G0;
+    if (!kMulti) G0 = view_single(A, blob);
+    auto gview = [&](int g) -> GroupView { return kMulti ? view_group(A.groups, g) : G0; };
+    const long long total = kMulti ? A.total_sims : A.n_sims;
     const bool exact = (A.mode == SSA_MODE_EXACT);
     const double kInf = __longlong_as_double(0x7FF0000000000000ll);
 
-    // this lane's simulation
+    // this lane's simulation: group grp, row within the group
+    int grp = 0;
     long long row = -1;
     uint32_t sim = 0;
     double t = 0.0;
@@ -143,17 +208,17 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
     uint32_t eb_att = 0;
     double eb_E[kBatch], eb_U[kBatch];
 
-    auto own_prop = [&](int j) -> double {
-        return Arith::prop(rinfo[j], __ldg(A.params + (size_t)row * M + j), X, kStride, lane);
+    auto own_prop = [&](const GroupView &G, int j) -> double {
+        return Arith::prop(G.rinfo[j], __ldg(G.params + (size_t)row * G.M + j), X, kStride, lane);
     };
-    auto lane_record = [&](int k) {
-        int *dst = A.samples + ((size_t)row * S + k) * (size_t)N;
-        for (int i = 0; i < N; ++i) dst[i] = X[i * kStride + lane];
+    auto lane_record = [&](const GroupView &G, int k) {
+        int *dst = G.samples + ((size_t)row * G.S + k) * (size_t)G.N;
+        for (int i = 0; i < G.N; ++i) dst[i] = X[i * kStride + lane];
     };
-    auto lane_build_tree = [&]() {
+    auto lane_build_tree = [&](const GroupView &G) {
         for (int l = 0; l < 32; ++l) {
             double s = 0.0;
-            for (int j = l; j < M; j += 32) s = s + own_prop(j);
+            for (int j = l; j < G.M; j += 32) s = s + own_prop(G, j);
             V[l * kStride + lane] = s;
         }
         for (int k = 1; k <= 5; ++k) {
@@ -174,9 +239,17 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
             base = __shfl_sync(kFull, base, 0);
             if (phase == P_NEED) {
                 const unsigned long long r = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
-                if (r < (unsigned long long)A.n_sims) {
-                    row = (long long)r;
-                    sim = (uint32_t)(A.sim_offset + row);
+                if (r < (unsigned long long)total) {
+                    if (kMulti) {
+                        int g = 0;
+                        while (g + 1 < A.n_groups && (long long)r >= A.groups[g + 1].first) ++g;
+                        grp = g;
+                    }
+                    const GroupView G = gview(grp);
+                    const int N = G.N, S = G.S;
+                    const double *T = G.T;
+                    row = (long long)r - G.first;
+                    sim = (uint32_t)(G.sim_offset + row);
                     t = 0.0;
                     ks = 0;
                     attempt = 0;
@@ -184,8 +257,8 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     leaps = rejected = ssa_steps = firings = 0;
                     eb_valid = false;
                     tnext = (S > 0) ? T[0] : kInf;
-                    for (int i = 0; i < N; ++i) X[i * kStride + lane] = A.x0[(size_t)row * N + i];
-                    if (exact) lane_build_tree();
+                    for (int i = 0; i < N; ++i) X[i * kStride + lane] = G.x0[(size_t)row * N + i];
+                    if (exact) lane_build_tree(G);
                     phase = P_TOP;
                 } else {
                     row = -1;
@@ -202,6 +275,12 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
             while (todo) {
                 const int L = __ffs(todo) - 1;
                 todo &= todo - 1;
+                const GroupView GL = gview(__shfl_sync(kFull, grp, L));
+                const int *rinfo = GL.rinfo, *nu_ptr = GL.nu_ptr, *nu_ent = GL.nu_ent, *tr_ptr = GL.tr_ptr,
+                          *tr_ent = GL.tr_ent, *hor = GL.hor;
+                const int N = GL.N, M = GL.M, S = GL.S;
+                const double *T = GL.T;
+                const double t_end = GL.t_end;
                 const long long rL = __shfl_sync(kFull, row, L);
                 const uint32_t sL = __shfl_sync(kFull, sim, L);
                 double tL = __shfl_sync(kFull, t, L);
@@ -213,8 +292,8 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                 long long fiL = fi0;
                 int stL = SSA_STATUS_OK;
                 int nphase = P_TOP, nleft = 0, nfirst = 0;
-                int *rowout = A.samples + (size_t)rL * S * (size_t)N;
-                const double *cL = A.params + (size_t)rL * M;
+                int *rowout = GL.samples + (size_t)rL * S * (size_t)N;
+                const double *cL = GL.params + (size_t)rL * M;
 
                 double tnL = __shfl_sync(kFull, tnext, L);
                 while (ksL < S && tnL <= tL) {
@@ -330,7 +409,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             }
                             attL = attL + 1;
                             double u_tau, u_sel;
-                            Arith::uniforms(A.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
+                            Arith::uniforms(GL.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
                             const double tau2 = (a0c > 0.0) ? Arith::tau_of(Arith::neglog(u_tau), a0c) : kInf;
                             const double t_stop = (ksL < S) ? tnL : t_end;
                             const double delta = t_stop - tL;
@@ -353,7 +432,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 if (w.crit[j]) {
                                     kj = (j == jc) ? 1 : 0;
                                 } else {
-                                    kj = Arith::poisson(w.a[j], tau, A.seed, sL, attL, (uint32_t)j, inv);
+                                    kj = Arith::poisson(w.a[j], tau, GL.seed, sL, attL, (uint32_t)j, inv);
                                     if (kj < 0) krej = 1;
                                     else if (kj > f64::kCountLimit) kover = 1;
                                 }
@@ -426,8 +505,12 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 
         // ---- lane-local part: exact-mode top of the loop
         if (exact && phase == P_TOP) {
+            const GroupView G = gview(grp);
+            const int S = G.S;
+            const double *T = G.T;
+            const double t_end = G.t_end;
             while (ks < S && tnext <= t) {
-                lane_record(ks++);
+                lane_record(G, ks++);
                 tnext = (ks < S) ? T[ks] : kInf;
             }
             if (t >= t_end) {
@@ -453,6 +536,11 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 
         // ---- lane-local part: one exact SSA step (direct method)
         if (phase == P_SSA) {
+            const GroupView G = gview(grp);
+            const int *nu_ptr = G.nu_ptr, *nu_ent = G.nu_ent, *dep_ptr = G.dep_ptr, *dep_ent = G.dep_ent;
+            const int M = G.M, S = G.S;
+            const double *T = G.T;
+            const double t_end = G.t_end;
             if (!first && !f64::nn_gt(t_end, t)) {
                 phase = P_TOP;
             } else {
@@ -476,7 +564,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 #pragma unroll
                         for (int q = 0; q < kBatch; ++q) {
                             double u1;
-                            Arith::uniforms(A.seed, sim, attempt + q, PURPOSE_SSA, u1, eb_U[q]);
+                            Arith::uniforms(G.seed, sim, attempt + q, PURPOSE_SSA, u1, eb_U[q]);
                             eb_E[q] = Arith::neglog(u1);
                         }
                     }
@@ -491,7 +579,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     const double tau = Arith::tau_of(E, a0);
                     const double t_new = t + tau;
                     while (ks < S && !f64::nn_ge(tnext, t_new)) {
-                        lane_record(ks++);
+                        lane_record(G, ks++);
                         tnext = (ks < S) ? T[ks] : kInf;
                     }
                     if (f64::nn_gt(t_new, t_end)) {
@@ -514,7 +602,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         double cum = 0.0;
                         int jf = -1, last = -1;
                         for (int j = cls; j < M; j += 32) {
-                            const double v = own_prop(j);
+                            const double v = own_prop(G, j);
                             cum = cum + v;
                             if (f64::nn_pos(v)) last = j;
                             if (f64::nn_gt(cum, target)) {
@@ -550,7 +638,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                     const int l = __ffs(m) - 1;
                                     m &= m - 1;
                                     double s = 0.0;
-                                    for (int j = l; j < M; j += 32) s = s + own_prop(j);
+                                    for (int j = l; j < M; j += 32) s = s + own_prop(G, j);
                                     V[l * kStride + lane] = s;
                                 }
 #pragma unroll
@@ -580,8 +668,9 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 
         // ---- finished simulations: remaining samples hold the final state
         if (phase == P_DONE) {
-            while (ks < S) lane_record(ks++);
-            if (A.stats != nullptr) {
+            const GroupView G = gview(grp);
+            while (ks < G.S) lane_record(G, ks++);
+            if (G.stats != nullptr) {
                 ssa_sim_stats st;
                 st.status = status;
                 st.reserved = 0;
@@ -591,7 +680,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                 st.firings = firings;
                 st.attempts = attempt;
                 st.t_final = t;
-                A.stats[row] = st;
+                G.stats[row] = st;
             }
             phase = P_NEED;
         }
@@ -606,22 +695,30 @@ inline size_t lane_smem_bytes(const ModelLayout &L, int block_warps)
     return model_smem_bytes(L) + lane::r16((f64::kInversionCap + 1) * 8) + (size_t)block_warps * lane::lane_warp_bytes(L.N, L.M);
 }
 
-template <class Arith>
+inline size_t lane_multi_bytes(int max_N, int max_M, int block_warps)
+{
+    return lane::r16((f64::kInversionCap + 1) * 8) + (size_t)block_warps * lane::lane_warp_bytes(max_N, max_M);
+}
+
+template <class Arith, bool kMulti>
 cudaError_t launch_lane_impl(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(lane::lane_kernel<Arith>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    lane::lane_kernel<Arith><<<grid, block_warps * 32, smem, s>>>(a);
+    lane::lane_kernel<Arith, kMulti><<<grid, block_warps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <class Arith>
+template <class Arith, bool kMulti>
 int lane_occupancy_impl(int block_warps, size_t smem)
 {
     int nb = 0;
-    if (cudaFuncSetAttribute(lane::lane_kernel<Arith>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lane::lane_kernel<Arith>, block_warps * 32, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lane::lane_kernel<Arith, kMulti>, block_warps * 32, smem) !=
+        cudaSuccess)
         return 0;
     return nb;
 }
