@@ -58,7 +58,8 @@ extern "C" {
 #define SSA_STATUS_REJECT_LIMIT 3 /* max_halvings negativity retries in one leap */
 #define SSA_STATUS_INVALID 4      /* the propensity sum a0 was not finite (bad rates) */
 
-/* job states (ssa_poll) */
+/* job / request states (ssa_poll, ssa_server_poll) */
+#define SSA_JOB_QUEUED 0
 #define SSA_JOB_RUNNING 1
 #define SSA_JOB_DONE 2
 #define SSA_JOB_FAILED 3
@@ -220,6 +221,56 @@ int ssa_wait(ssa_job_t job);
 int ssa_fetch(ssa_job_t job, int32_t *samples, ssa_sim_stats *stats);
 /* Wait for the job and free everything it owns. */
 int ssa_release_job(ssa_job_t job);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of simulation requests                   */
+/* ------------------------------------------------------------------ */
+/* A request is one network and one batch of simulations, with HOST inputs.
+ * A dispatcher thread admits queued requests in arrival order whenever one
+ * of n_streams stream slots is free and the request's device footprint
+ * (inputs + outputs) fits the HBM budget still unused; the requests
+ * admitted together run as one multi-network launch, and launches on
+ * different slots overlap on the device.  Results stay resident in device
+ * memory until ssa_server_fetch copies them out and frees them, returning
+ * their bytes to the budget (a client that never fetches keeps its memory).
+ * Simulation r of a request uses the random stream (request seed, r), so a
+ * request's result is the same alone and in any mix. */
+typedef struct ssa_server *ssa_server_t;
+
+typedef struct {
+    int64_t max_device_bytes; /* HBM budget for admitted requests; 0 = 80% of free memory at creation */
+    int32_t n_streams;        /* launches in flight (1..16), default 4 */
+    int32_t max_batch;        /* requests per launch (1..256), default 16 */
+    ssa_options opts;         /* applied to every request; default precision SSA_FAST */
+} ssa_server_config;
+
+typedef struct {
+    int32_t state;      /* SSA_JOB_QUEUED, _RUNNING, _DONE or _FAILED */
+    int32_t batch_size; /* requests in the launch that ran this one */
+    double t_submit;    /* seconds since server creation */
+    double t_admit;     /* -1 until admitted */
+    double t_done;      /* -1 until the launch completed */
+} ssa_request_info;
+
+void ssa_server_default_config(ssa_server_config *cfg);
+/* Create a server on the current device (models submitted to it must live there). */
+int ssa_server_create(const ssa_server_config *cfg, ssa_server_t *out);
+/* Queue a request; inputs are copied before the call returns.  *ticket
+ * identifies it.  SSA_ENOMEM if its footprint exceeds the whole budget. */
+int ssa_server_submit(ssa_server_t srv, ssa_model_t model, int64_t n_sims, const double *params,
+                      const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
+                      uint64_t seed, int64_t *ticket);
+int ssa_server_poll(ssa_server_t srv, int64_t ticket, ssa_request_info *info);
+int ssa_server_wait(ssa_server_t srv, int64_t ticket, ssa_request_info *info);
+/* Wait for the request, copy samples [n_sims][n_samples][N] and stats
+ * [n_sims] (either may be NULL) to HOST memory, free its device memory and
+ * forget the ticket. */
+int ssa_server_fetch(ssa_server_t srv, int64_t ticket, int32_t *samples, ssa_sim_stats *stats);
+/* Launches issued so far, requests waiting for admission, admitted bytes. */
+int ssa_server_stats(ssa_server_t srv, int64_t *launches, int64_t *queued, int64_t *device_bytes_in_use);
+/* Finish queued and running requests, free everything. */
+int ssa_server_destroy(ssa_server_t srv);
+const char *ssa_server_last_error(void);
 
 /* Message describing the last failed call on this thread ("" if none). */
 const char *ssa_last_error(void);

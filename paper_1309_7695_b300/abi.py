@@ -28,6 +28,7 @@ SSA_STATUS_OVERFLOW = 2
 SSA_STATUS_REJECT_LIMIT = 3
 SSA_STATUS_INVALID = 4
 
+SSA_JOB_QUEUED = 0
 SSA_JOB_RUNNING = 1
 SSA_JOB_DONE = 2
 SSA_JOB_FAILED = 3
@@ -44,6 +45,8 @@ EXPORTED = [
     "ssa_default_options", "ssa_load_model", "ssa_free_model", "ssa_model_info",
     "ssa_simulate_dev", "ssa_simulate_dev_noalloc", "ssa_simulate_multi_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
     "ssa_release_job", "ssa_last_error", "ssa_abi_version",
+    "ssa_server_default_config", "ssa_server_create", "ssa_server_submit", "ssa_server_poll", "ssa_server_wait",
+    "ssa_server_fetch", "ssa_server_stats", "ssa_server_destroy", "ssa_server_last_error",
 ]
 
 
@@ -77,6 +80,16 @@ class Options(ctypes.Structure):
         ("max_halvings", ctypes.c_int32), ("layout", ctypes.c_int32), ("max_attempts", ctypes.c_int64),
         ("block_warps", ctypes.c_int32), ("sims_per_warp", ctypes.c_int32),
     ]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_device_bytes", ctypes.c_int64), ("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("opts", Options)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 STATS_DTYPE = np.dtype([
@@ -115,8 +128,20 @@ def lib():
     L.ssa_last_error.argtypes = []
     L.ssa_last_error.restype = ctypes.c_char_p
     L.ssa_abi_version.argtypes = []
+    L.ssa_server_default_config.argtypes = [ctypes.POINTER(ServerConfig)]
+    L.ssa_server_default_config.restype = None
+    L.ssa_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    L.ssa_server_submit.argtypes = [vp, vp, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(i64)]
+    L.ssa_server_poll.argtypes = [vp, i64, ctypes.POINTER(RequestInfo)]
+    L.ssa_server_wait.argtypes = [vp, i64, ctypes.POINTER(RequestInfo)]
+    L.ssa_server_fetch.argtypes = [vp, i64, vp, vp]
+    L.ssa_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.ssa_server_destroy.argtypes = [vp]
+    L.ssa_server_last_error.argtypes = []
+    L.ssa_server_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("ssa_default_options", "ssa_last_error"):
+        if name not in ("ssa_default_options", "ssa_last_error", "ssa_server_default_config",
+                        "ssa_server_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -289,3 +314,68 @@ def simulate_host(network, params, x0, t_end, sample_times, seed=0, opts=None):
             j.release()
     finally:
         m.close()
+
+
+def _scheck(rc):
+    if rc != SSA_OK:
+        raise SsaError(rc, lib().ssa_server_last_error().decode())
+
+
+class Server:
+    """Continuous-batching request server (ssa_server_*)."""
+
+    def __init__(self, max_device_bytes=0, n_streams=4, max_batch=16, opts=None):
+        c = ServerConfig()
+        lib().ssa_server_default_config(ctypes.byref(c))
+        c.max_device_bytes = int(max_device_bytes)
+        c.n_streams = int(n_streams)
+        c.max_batch = int(max_batch)
+        if opts is not None:
+            c.opts = opts
+        h = ctypes.c_void_p()
+        _scheck(lib().ssa_server_create(ctypes.byref(c), ctypes.byref(h)))
+        self.handle = h
+        self._shapes = {}
+
+    def submit(self, model, params, x0, t_end, sample_times, seed=0) -> int:
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        x0 = np.ascontiguousarray(x0, dtype=np.int32)
+        T = np.ascontiguousarray(sample_times, dtype=np.float64)
+        t = ctypes.c_int64()
+        _scheck(lib().ssa_server_submit(self.handle, model.handle, int(params.shape[0]), _ptr(params), _ptr(x0),
+                                        float(t_end), _ptr(T), int(T.size), int(seed), ctypes.byref(t)))
+        self._shapes[t.value] = (int(params.shape[0]), int(T.size), model.n_species)
+        return t.value
+
+    def poll(self, ticket) -> RequestInfo:
+        info = RequestInfo()
+        _scheck(lib().ssa_server_poll(self.handle, int(ticket), ctypes.byref(info)))
+        return info
+
+    def wait(self, ticket) -> RequestInfo:
+        info = RequestInfo()
+        _scheck(lib().ssa_server_wait(self.handle, int(ticket), ctypes.byref(info)))
+        return info
+
+    def fetch(self, ticket):
+        n, S, N = self._shapes.pop(ticket)
+        samples = np.empty((n, S, N), dtype=np.int32)
+        stats = np.empty(n, dtype=STATS_DTYPE)
+        _scheck(lib().ssa_server_fetch(self.handle, int(ticket), _ptr(samples), _ptr(stats)))
+        return samples, stats
+
+    def stats(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _scheck(lib().ssa_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"launches": a.value, "queued": b.value, "device_bytes_in_use": c.value}
+
+    def close(self):
+        if self.handle:
+            lib().ssa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -27,6 +27,7 @@ UNITS = {
     "kernel_warp_f64.cu": ["-fmad=false"],
     "kernel_lane_f64.cu": ["-fmad=false"],
     "kernel_lane_fast.cu": [],
+    "server.cu": [],
 }
 
 
