@@ -181,6 +181,138 @@ def run_reference(args):
     return 0
 
 
+def run_hetero(args):
+    """Heterogeneous batch (8 networks of 8..512 reactions, log-uniform
+    replicates and horizons, fast mode): one launch per network on one
+    stream against one autotuned persistent multi-network launch."""
+    import torch
+
+    from paper_1309_7695_b300 import abi, autotune
+
+    dev = torch.device("cuda:0")
+    groups = inputs.hetero_groups(args.hetero_sims, seed=0)
+    models, gd = {}, []
+    for k, b in enumerate(groups):
+        if b.network.name not in models:
+            models[b.network.name] = abi.Model(b.network)
+        n, N, S = b.n_sims, b.network.n_species, len(b.sample_times)
+        gd.append({"model": models[b.network.name], "params": torch.from_numpy(b.params).to(dev),
+                   "x0": torch.from_numpy(b.x0).to(dev), "sample_times": torch.from_numpy(b.sample_times).to(dev),
+                   "samples": torch.empty((n, S, N), dtype=torch.int32, device=dev),
+                   "stats": torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev),
+                   "t_end": b.t_end, "seed": 100 + k})
+    cap = WORKLOAD["max_attempts"]
+
+    def totals():
+        f = st = 0.0
+        for g in gd:
+            s = g["stats"].cpu().numpy().view(abi.STATS_DTYPE)
+            f += float(s["firings"].sum())
+            st += float(s["leaps"].sum() + s["ssa_steps"].sum())
+        return f, st
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    o = abi.ssa_default_options(precision=abi.SSA_FAST, max_attempts=cap)
+
+    def plain():
+        for g in gd:
+            abi.ssa_simulate_dev(g["model"], g["params"], g["x0"], g["t_end"], g["sample_times"], g["samples"],
+                                 g["stats"], seed=g["seed"], opts=o)
+
+    t0 = time.perf_counter()
+    ordered, topts, costs = autotune.plan(gd, precision=abi.SSA_FAST)
+    t_plan = time.perf_counter() - t0
+    topts.max_attempts = cap
+    t_plain = timed(plain)
+    f_plain, s_plain = totals()
+    t_multi = timed(lambda: abi.ssa_simulate_multi_dev(ordered, opts=topts))
+    f_multi, s_multi = totals()
+    line = {"metric": METRIC, "workload": "hetero", "value": f_multi / t_multi, "unit": "firings/s",
+            "sim_steps_per_s": s_multi / t_multi, "plain_value": f_plain / t_plain,
+            "plain_sim_steps_per_s": s_plain / t_plain, "speedup_vs_plain": t_plain / t_multi,
+            "seconds_persistent": t_multi, "seconds_plain": t_plain, "seconds_planning": t_plan,
+            "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'", "data": "synthetic",
+            "config": {"workload": f"heterogeneous batch: {len(gd)} groups over 8 random networks (8..512 reactions, "
+                                   f"species = reactions/2), replicates logU[16,8192], t_end logU[10,1000], 101 samples",
+                       "n_sims": sum(int(g['params'].shape[0]) for g in gd), "max_attempts": cap,
+                       "schedule": f"autotuned: most expensive group first, block_warps={topts.block_warps}, "
+                                   f"sims_per_warp={topts.sims_per_warp}"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    """Served request stream: Poisson arrivals, continuous batching, p50/p99."""
+    import torch  # noqa: F401  (initialises the CUDA context used by the server)
+
+    from paper_1309_7695_b300 import abi
+
+    rng = np.random.default_rng(7)
+    pool = []
+    for k in range(args.serve_networks):
+        m = int(np.floor(np.exp(rng.uniform(np.log(8), np.log(513)))))
+        n = int(rng.integers(4, min(256, 2 * m) + 1))
+        net = inputs.random_network(n, m, 500 + k)
+        pool.append((net, abi.Model(net)))
+    cap = args.serve_cap
+    opts = abi.ssa_default_options(precision=abi.SSA_FAST, max_attempts=cap)
+    results = []
+    for lam in args.serve_rates:
+        srv = abi.Server(n_streams=4, max_batch=16, opts=opts)
+        reqs = []
+        for r in range(args.serve_requests):
+            net, model = pool[int(rng.integers(len(pool)))]
+            reps = int(np.floor(np.exp(rng.uniform(0.0, np.log(4097)))))
+            t_end = float(np.exp(rng.uniform(0.0, np.log(500.0))))
+            S = int(rng.integers(10, 201))
+            params = inputs.log_uniform(rng, 1e-4, 1.0, (reps, net.n_reactions))
+            x0 = rng.integers(0, 1001, size=(reps, net.n_species)).astype(np.int32)
+            reqs.append((model, params, x0, t_end, inputs.uniform_sample_times(t_end, S), 10_000 + r))
+        gaps = rng.exponential(1.0 / lam, size=len(reqs))
+        t_start = time.perf_counter()
+        tickets, next_t = [], 0.0
+        for (model, params, x0, t_end, T, seed), gap in zip(reqs, gaps):
+            next_t += gap
+            delay = next_t - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(model, params, x0, t_end, T, seed))
+        lat, fir, steps, bsz = [], 0.0, 0.0, []
+        for t in tickets:
+            info = srv.wait(t)
+            _, st = srv.fetch(t)
+            lat.append(info.t_done - info.t_submit)
+            bsz.append(info.batch_size)
+            fir += float(st["firings"].sum())
+            steps += float(st["leaps"].sum() + st["ssa_steps"].sum())
+        wall = time.perf_counter() - t_start
+        launches = srv.stats()["launches"]
+        srv.close()
+        lat = np.asarray(lat)
+        results.append({"lambda_per_s": lam, "requests": len(reqs), "p50_s": float(np.percentile(lat, 50)),
+                        "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+                        "firings_per_s": fir / wall, "sim_steps_per_s": steps / wall, "wall_s": wall,
+                        "launches": launches, "mean_batch": float(np.mean(bsz))})
+        print(json.dumps({"served": results[-1]}), flush=True)
+    line = {"metric": METRIC, "workload": "served", "value": results[0]["p99_s"], "unit": "s (p99 latency)",
+            "higher_is_better": False, "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'", "data": "synthetic",
+            "rates": results,
+            "config": {"workload": f"served stream: Poisson arrivals, {args.serve_requests} requests per rate, "
+                                   f"pool of {args.serve_networks} random networks (M logU-int[8,512], "
+                                   f"N U-int[4,min(256,2M)]), replicates logU-int[1,4096], t_end logU[1,500], "
+                                   f"S U-int[10,200]", "max_attempts": cap, "server": "4 stream slots, 16 per batch"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +325,12 @@ def main():
     # profiling / sweep knobs; the reported benchmark uses the defaults
     ap.add_argument("--sims", type=int, default=None, help="override the simulations per GPU (profiling)")
     ap.add_argument("--cap", type=int, default=None, help="override the per-simulation attempt cap (profiling)")
+    ap.add_argument("--workload", default="rand32x64", choices=["rand32x64", "hetero", "served"])
+    ap.add_argument("--hetero-sims", type=int, default=20000)
+    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-networks", type=int, default=32)
+    ap.add_argument("--serve-cap", type=int, default=1 << 18)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 100.0, 1000.0])
     args = ap.parse_args()
     if args.sims is not None:
         WORKLOAD["n_sims"] = args.sims
@@ -200,6 +338,10 @@ def main():
         WORKLOAD["max_attempts"] = args.cap
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "hetero":
+        return run_hetero(args)
+    if args.workload == "served":
+        return run_served(args)
 
     import torch
     import torch.distributed as dist

@@ -166,7 +166,9 @@ def uniform_sample_times(t_end: float, n_samples: int) -> np.ndarray:
     if n_samples == 1:
         return np.asarray([t_end], dtype=np.float64)
     k = np.arange(n_samples, dtype=np.float64)
-    return (k * t_end) / float(n_samples - 1)
+    T = (k * t_end) / float(n_samples - 1)
+    T[-1] = t_end          # (S-1) t_end / (S-1) can round one ulp above t_end
+    return np.minimum(T, t_end)
 
 
 def mm_batch(n_sims: int = 1024, seed: int = 0, t_end: float = 10.0, n_samples: int = 11,
