@@ -8,11 +8,16 @@ t_end = 100 with 101 sample times, epsilon = 0.03, n_c = 10, FP64 reference
 mode (bit-exact with the CPU oracle).  Every simulation runs to t_end or to a
 budget of 2^20 leap attempts + SSA steps.
 
-A step is one launch that simulates the whole batch (inputs resident in
-HBM).  Reported: reaction firings/s (value) and sim-steps/s (accepted leaps
-+ SSA events), the same metric end to end through the host-buffer C ABI
-(e2e), the roofline position of the simulation kernel, and the CPU oracle
-on a bounded sample of the same workload (cpu_baseline).
+A step simulates one such batch with its own seed (inputs resident in
+HBM).  By default the K timed steps run as K batches in flight in one
+persistent launch of the engine (--schedule multi), so the long-running
+simulations of one batch overlap the bulk of the next; --schedule serial
+times one launch per batch, one after another.  Reported: reaction
+firings/s (value) and sim-steps/s (accepted leaps + SSA events), the same
+batches in fast mode, the same metric end to end through the host-buffer
+C ABI with one job per step in flight (e2e), the roofline position of the
+simulation kernel against the FP64 issue rate, and the CPU oracle on a
+bounded sample of the same workload (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
 Multi-GPU (torchrun, one rank per GPU): each rank simulates its own 65,536
@@ -40,9 +45,8 @@ from paper_1309_7695_b300 import inputs  # noqa: E402
 METRIC = "reaction firings/s & sim-steps/s (KS-matched) vs plain FP64; serve p50/p99"
 WORKLOAD = dict(n_species=32, n_reactions=64, n_sims=65536, t_end=100.0, n_samples=101,
                 x0_max=1000, eps=0.03, n_c=10, max_attempts=1 << 20, network_seed=0)
-FP64_PEAK_OPS = 148 * 2 * 2.032e9  # FP64 FMA-pipe ops/s: 148 SMs x 2/clk x 2032 MHz
 L2_FLUSH_BYTES = 256 << 20
-KERNEL_NAMES = {0: "lane_f64_kernel", 1: "warp_f64_kernel", 2: "lane_f64_kernel"}
+KERNEL_NAMES = {0: "lane_kernel<RefArith, false>", 1: "warp_f64_kernel", 2: "lane_kernel<RefArith, false>"}
 
 
 def algorithmic_fp64_ops(stats, M, N, nnz):
@@ -119,8 +123,7 @@ def config_dict(extra=None):
                      f"{w['n_sims']} parameterizations, t_end={w['t_end']:g}, {w['n_samples']} sample times",
          "n_species": w["n_species"], "n_reactions": w["n_reactions"], "n_sims_per_gpu": w["n_sims"],
          "t_end": w["t_end"], "n_samples": w["n_samples"], "eps": w["eps"], "n_c": w["n_c"],
-         "max_attempts": w["max_attempts"], "mode": "tau-leap (CGP) + SSA fallback", "precision": "fp64-ref",
-         "l2": "flushed between timed steps (256 MB write)"}
+         "max_attempts": w["max_attempts"], "mode": "tau-leap (CGP) + SSA fallback", "precision": "fp64-ref"}
     if extra:
         d.update(extra)
     return d
@@ -313,6 +316,25 @@ def run_served(args):
     return 0
 
 
+def fp64_peak_ops(torch, dev):
+    """FP64 issue peak of this GPU, measured live: a cuBLAS DGEMM (2 N^3
+    flops, one multiply-add per operation counted once), best of 5."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return float(n) ** 3 / best
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,8 +342,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--layout", type=int, default=0, help="0 auto, 1 warp per simulation, 2 lane per simulation")
+    ap.add_argument("--schedule", default="multi", choices=["multi", "streams", "serial"],
+                    help="multi: the steps' batches in flight in one persistent launch; streams: one launch per "
+                         "batch on its own stream; serial: one launch per batch, one after another")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fast", action="store_true")
     # profiling / sweep knobs; the reported benchmark uses the defaults
     ap.add_argument("--sims", type=int, default=None, help="override the simulations per GPU (profiling)")
     ap.add_argument("--cap", type=int, default=None, help="override the per-simulation attempt cap (profiling)")
@@ -369,43 +395,75 @@ def main():
     p = torch.from_numpy(batch.params).to(dev)
     x = torch.from_numpy(batch.x0).to(dev)
     T = torch.from_numpy(batch.sample_times).to(dev)
-    out = torch.empty((n, S, N), dtype=torch.int32, device=dev)
-    st = torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    nb = max(args.steps, args.warmup) if args.schedule != "serial" else 1
+    outs = [torch.empty((n, S, N), dtype=torch.int32, device=dev) for _ in range(nb)]
+    sts = [torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev) for _ in range(nb)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    opts = abi.ssa_default_options(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"], max_attempts=WORKLOAD["max_attempts"],
-                                   layout=args.layout)
     stream = torch.cuda.current_stream()
+    side = [torch.cuda.Stream(device=dev) for _ in range(nb)] if args.schedule == "streams" else []
 
-    def one(seed):
-        abi.ssa_simulate_dev(model, p, x, batch.t_end, T, out, st, seed=seed, opts=opts, sim_offset=sim_offset,
-                             stream=stream)
+    def options(precision):
+        return abi.ssa_default_options(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"],
+                                       max_attempts=WORKLOAD["max_attempts"], layout=args.layout, precision=precision)
 
-    for w in range(args.warmup):
-        one(5000 + w)
-    torch.cuda.synchronize()
+    def run(seeds, precision):
+        """Simulate one batch per seed (the steps); returns (seconds, [stats], launches)."""
+        o = options(precision)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats, launches = [], 0
+        if args.schedule == "multi":
+            groups = [dict(model=model, params=p, x0=x, sample_times=T, samples=outs[k], stats=sts[k],
+                           t_end=batch.t_end, seed=sd, sim_offset=sim_offset) for k, sd in enumerate(seeds)]
+            e0.record(stream)
+            abi.ssa_simulate_multi_dev(groups, opts=o, stream=stream)
+            e1.record(stream)
+            launches = 1
+            torch.cuda.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3
+            stats = [sts[k].cpu().numpy().view(abi.STATS_DTYPE).reshape(-1) for k in range(len(seeds))]
+        elif args.schedule == "streams":
+            e0.record(stream)
+            for k, sd in enumerate(seeds):
+                side[k].wait_event(e0)
+                abi.ssa_simulate_dev(model, p, x, batch.t_end, T, outs[k], sts[k], seed=sd, opts=o,
+                                     sim_offset=sim_offset, stream=side[k])
+                stream.wait_stream(side[k])
+            e1.record(stream)
+            launches = len(seeds)
+            torch.cuda.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3
+            stats = [sts[k].cpu().numpy().view(abi.STATS_DTYPE).reshape(-1) for k in range(len(seeds))]
+        else:
+            dt = 0.0
+            for sd in seeds:
+                flush.fill_(sd & 0xFF)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                abi.ssa_simulate_dev(model, p, x, batch.t_end, T, outs[0], sts[0], seed=sd, opts=o,
+                                     sim_offset=sim_offset, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dt += e0.elapsed_time(e1) / 1e3
+                stats.append(sts[0].cpu().numpy().view(abi.STATS_DTYPE).reshape(-1).copy())
+                launches += 1
+        return dt, stats, launches
+
+    peak_ops = fp64_peak_ops(torch, dev)
+    run([5000 + w for w in range(args.warmup)], abi.SSA_FP64_REF)
 
     clocks = ClockSampler(local)
+    flush.fill_(1)
+    barrier()
+    torch.cuda.synchronize()
     clocks.start()
-    times_ms, fir, simsteps, ops, capped = [], 0.0, 0.0, 0.0, 0
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        one(1000 + k)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        times_ms.append(e0.elapsed_time(e1))
-        s = st.cpu().numpy().view(abi.STATS_DTYPE).reshape(-1)
-        fir += float(s["firings"].sum())
-        simsteps += float(s["leaps"].sum() + s["ssa_steps"].sum())
-        ops += algorithmic_fp64_ops(s, M, N, nnz)
-        capped += int((s["status"] == abi.SSA_STATUS_STEP_LIMIT).sum())
+    local_t, stats, launches = run([1000 + k for k in range(args.steps)], abi.SSA_FP64_REF)
     clk = clocks.stop()
-    local_t = sum(times_ms) / 1e3
+    barrier()
+    fir = sum(float(s["firings"].sum()) for s in stats)
+    simsteps = sum(float(s["leaps"].sum() + s["ssa_steps"].sum()) for s in stats)
+    ops = sum(algorithmic_fp64_ops(s, M, N, nnz) for s in stats)
+    capped = sum(int((s["status"] == abi.SSA_STATUS_STEP_LIMIT).sum()) for s in stats)
     t_max = local_t
     tot = torch.tensor([fir, simsteps, ops, float(capped)], dtype=torch.float64, device=dev)
     if world > 1:
@@ -415,24 +473,43 @@ def main():
         t_max = float(tt.item())
     fir, simsteps, ops, capped = (float(v) for v in tot.tolist())
 
+    fast = None
+    if not args.no_fast:
+        # the same batches in fast mode (FP32 propensities and Poisson sampler; its accuracy
+        # against the FP64 mode is established by the coupled KS / moment tests)
+        ft, fstats, _ = run([1000 + k for k in range(args.steps)], abi.SSA_FAST)
+        ff = sum(float(s["firings"].sum()) for s in fstats)
+        fsteps = sum(float(s["leaps"].sum() + s["ssa_steps"].sum()) for s in fstats)
+        ftot = torch.tensor([ff, fsteps], dtype=torch.float64, device=dev)
+        if world > 1:
+            ftt = torch.tensor([ft], dtype=torch.float64, device=dev)
+            dist.all_reduce(ftt, op=dist.ReduceOp.MAX)
+            dist.all_reduce(ftot, op=dist.ReduceOp.SUM)
+            ft = float(ftt.item())
+        ff, fsteps = (float(v) for v in ftot.tolist())
+        fast = {"value": ff / ft, "unit": "firings/s", "sim_steps_per_s": fsteps / ft, "ms_per_step": ft * 1e3 / args.steps,
+                "vs_fp64": (ff / ft) / (fir / t_max), "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'"}
+
     e2e = None
     if not args.no_e2e:
-        # host-buffer path: pinned inputs -> ssa_submit_batch (H2D inside) -> ssa_fetch (D2H) each step
+        # host-buffer path: pinned inputs -> ssa_submit_batch (H2D inside, one job and stream per
+        # step, all in flight together) -> ssa_fetch (D2H) of every step's samples and counters
         hp = torch.from_numpy(batch.params).pin_memory().numpy()
         hx = torch.from_numpy(batch.x0).pin_memory().numpy()
         hT = batch.sample_times.copy()
-        hs = torch.empty((n, S, N), dtype=torch.int32).pin_memory().numpy()
-        hst = np.zeros(n, dtype=abi.STATS_DTYPE)
-        e2e_t, e2e_f = 0.0, 0.0
-        for k in range(args.steps):
-            barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            job = abi.ssa_submit_batch(model, hp, hx, batch.t_end, hT, seed=1000 + k, opts=opts)
-            job.fetch(hs, hst)
+        hs = [torch.empty((n, S, N), dtype=torch.int32).pin_memory().numpy() for _ in range(args.steps)]
+        hst = [np.zeros(n, dtype=abi.STATS_DTYPE) for _ in range(args.steps)]
+        o = options(abi.SSA_FP64_REF)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        jobs = [abi.ssa_submit_batch(model, hp, hx, batch.t_end, hT, seed=1000 + k, opts=o) for k in range(args.steps)]
+        for k, job in enumerate(jobs):
+            job.fetch(hs[k], hst[k])
+        e2e_t = time.perf_counter() - t0
+        for job in jobs:
             job.release()
-            e2e_t += time.perf_counter() - t0
-            e2e_f += float(hst["firings"].sum())
+        e2e_f = sum(float(h["firings"].sum()) for h in hst)
         et = torch.tensor([e2e_t, e2e_f], dtype=torch.float64, device=dev)
         if world > 1:
             mx = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
@@ -442,23 +519,31 @@ def main():
             e2e_f = float(et[1].item())
         e2e = {"value": e2e_f / e2e_t, "unit": "firings/s",
                "h2d_bytes_per_step": int(hp.nbytes + hx.nbytes + hT.nbytes),
-               "d2h_bytes_per_step": int(hs.nbytes + hst.nbytes)}
+               "d2h_bytes_per_step": int(hs[0].nbytes + hst[0].nbytes),
+               "schedule": "one ssa_submit_batch job (own stream) per step, all in flight"}
 
     if rank == 0:
-        kernel_s = local_t / args.steps
-        achieved = ops / world / args.steps / kernel_s
+        kernel_s = local_t / launches
+        achieved = ops / world / launches / kernel_s
+        sched = {"multi": f"the {args.steps} steps' batches in flight in one persistent launch",
+                 "streams": f"one launch per step on {args.steps} concurrent streams",
+                 "serial": "one launch per step, one after another, L2 flushed between"}[args.schedule]
         line = {"metric": METRIC, "value": fir / t_max, "unit": "firings/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded random network and parameter sweep)",
                 "sim_steps_per_s": simsteps / t_max,
                 "config": config_dict({"parallelism": f"dp{world} (independent simulation shards)",
-                                       "capped_fraction": capped / (world * n * args.steps)}),
-                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
-                             "unit": "TFP64-op/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
-                             "kernel": KERNEL_NAMES.get(args.layout, "lane_f64_kernel"),
-                             "peak_source": "148 SMs x 2 FP64 ops/clk x 2032 MHz"},
-                "clocks": clk, "gpu_launches": args.steps, "e2e": e2e}
+                                       "capped_fraction": capped / (world * n * args.steps), "schedule": sched,
+                                       "l2": "each step reads 41 MB of inputs and writes 847 MB of samples (> L2); "
+                                             "L2 flushed before the timed region"}),
+                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                             "unit": "T FP64-op/s", "frac": achieved / peak_ops, "traffic": None,
+                             "kernel": ("lane_kernel<RefArith, true>" if args.schedule == "multi"
+                                        else KERNEL_NAMES.get(args.layout, "lane_kernel<RefArith, false>")),
+                             "peak_source": "FP64 multiply-add rate of a cuBLAS DGEMM (4096^3) measured in this run, "
+                                            "one operation per multiply-add"},
+                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "fast_mode": fast}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_rate(batch)
         print(json.dumps(line), flush=True)

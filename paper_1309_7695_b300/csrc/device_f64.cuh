@@ -77,6 +77,12 @@ __device__ __forceinline__ double u53_to_double(unsigned long long v)
     return __longlong_as_double((long long)(((unsigned long long)(1023 + p) << 52) | frac));
 }
 __device__ __forceinline__ double count_to_double(int x) { return u53_to_double((unsigned long long)(unsigned)x); }
+// Exact conversion of a small signed integer (|v| < 2^31), from bits.
+__device__ __forceinline__ double small_to_double(int v)
+{
+    const double m = u53_to_double((unsigned long long)(v < 0 ? -(long long)v : (long long)v));
+    return v < 0 ? __longlong_as_double(__double_as_longlong(m) | (long long)0x8000000000000000ull) : m;
+}
 
 // ------------------------------------------------------ log, exp, log k!
 // ln 2 split: the high part keeps 32 significant bits so that e * LN2_HI
@@ -183,61 +189,142 @@ __device__ __forceinline__ double dlnfact(long long k)
 constexpr long long kCountLimit = 1ll << 40;
 constexpr int kInversionCap = 100;
 constexpr int kPtrsMaxIters = 1000;
+// entries of the 1/k table: k = 0..kInversionCap+1 (the inversion loop reads
+// one entry ahead of the term it adds)
+constexpr int kInvTable = kInversionCap + 2;
 
-// k ~ Poisson(lam) on the stream (sim, attempt, reaction j).  Means below 10:
-// inversion by sequential search with one uniform (stop early once a term no
-// longer changes the running cdf).  Means >= 10: PTRS, transformed rejection
-// with squeeze (Hormann 1993), one stream block per iteration.  Returns -1
-// if PTRS exhausts its iteration cap and kCountLimit + 1 for a draw above
-// kCountLimit.  `inv` holds 1/k for k = 1..kInversionCap (correctly rounded,
-// so identical to dividing).
-__device__ __forceinline__ long long poisson(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
-                                             uint32_t j, const double *__restrict__ inv)
+// The inversion draw of reaction j uses the first word pair of block 0 of
+// its stream.
+__device__ __forceinline__ double inversion_uniform(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
 {
-    if (!(lam > 0.0)) return 0;
-    if (!(lam < 0x1p40)) return kCountLimit + 1;
-    if (lam < 10.0) {
-        const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, 0);
-        const double u = u01(w.x, w.y);
-        double p = dexp(-lam);
-        double F = p;
-        long long k = 0;
-        while (u > F && k < kInversionCap) {
-            k = k + 1;
-            p = (p * lam) * inv[k];
-            const double Fn = F + p;
-            if (Fn == F) break;
-            F = Fn;
-        }
-        return k;
+    const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, 0);
+    return u01(w.x, w.y);
+}
+
+// True only when inversion certainly returns k = 0 for this (lam, u), that
+// is u <= dexp(-lam), decided without evaluating dexp.  For 0 < lam < 1,
+// e^-lam >= 1 - lam, and dexp(-lam) is within 2^-46 of e^-lam there (its
+// Cody-Waite reduction, Taylor truncation and 15 rounded operations each
+// contribute far less), while RN(1 - lam) is within 2^-54 of 1 - lam.  So
+// dexp(-lam) >= RN(1 - lam) - 2^-45 > RN(RN(1 - lam) - 2^-40), and any u at
+// or below that bound gives k = 0 exactly as the full loop would.  The test
+// is a sufficient condition only; otherwise the caller runs the loop.
+__device__ __forceinline__ bool inversion_zero_sure(double lam, double u)
+{
+    const double lo = (1.0 - lam) - 0x1p-40;
+    return lo > 0.0 && nn_ge(lo, u);
+}
+
+// Inversion by sequential search for 0 < lam < 10: the smallest k with
+// u <= F(k), where p_0 = dexp(-lam), p_k = (p_{k-1} lam) / k and F(k) =
+// F(k-1) + p_k, stopping once a term no longer changes F (the rest of the
+// tail is below the rounding of F) or at kInversionCap.  `inv` holds
+// RN(1/k), so multiplying by it equals dividing by k.  The next term is
+// formed before the current one is tested, so the multiply chain of p and
+// the add chain of F overlap; u, F and p are positive, so the comparisons
+// run on their bit patterns (same order as the IEEE comparison).
+__device__ __forceinline__ long long inversion_draw(double lam, double u, const double *__restrict__ inv)
+{
+    double p = dexp(-lam);
+    double F = p;
+    double pn = (p * lam) * inv[1];
+    long long k = 0;
+    while (nn_gt(u, F) && k < kInversionCap) {
+        k = k + 1;
+        p = pn;
+        pn = (p * lam) * inv[k + 1];
+        const double Fn = F + p;
+        if (dbits(Fn) == dbits(F)) break;
+        F = Fn;
     }
+    return k;
+}
+
+// K * 2^-53 for an integer 0 < K < 2^53, exactly, from bits.
+__device__ __forceinline__ double scaled53(unsigned long long K)
+{
+    return __longlong_as_double(__double_as_longlong(u53_to_double(K)) - (53ll << 52));
+}
+
+// floor(x) of a finite double as an integer, from bits (exact; the same
+// value as the rounding instruction followed by a conversion).  |x| >= 2^62
+// is returned as +-2^62: callers only test such values for sign and for
+// exceeding the count limit.
+__device__ __forceinline__ long long floor_to_ll(double x)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;   // x = 1.f * 2^e
+    const bool neg = bits < 0;
+    if (e < 0) return (neg && (bits << 1) != 0) ? -1 : 0;   // |x| < 1
+    if (e >= 62) return neg ? -(1ll << 62) : (1ll << 62);
+    const unsigned long long mant = ((unsigned long long)bits & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    long long t;
+    bool frac;
+    if (e >= 52) {
+        t = (long long)(mant << (e - 52));
+        frac = false;
+    } else {
+        t = (long long)(mant >> (52 - e));
+        frac = (mant & ((1ull << (52 - e)) - 1)) != 0;
+    }
+    return neg ? -(t + (frac ? 1 : 0)) : t;
+}
+
+// PTRS, transformed rejection with squeeze (Hormann 1993), for lam >= 10:
+// one stream block per iteration (block index = iteration).  Returns -1 if
+// it exhausts kPtrsMaxIters and kCountLimit + 1 for a draw above
+// kCountLimit.
+//
+// Every step that is exact in IEEE arithmetic runs on the integer pipe with
+// the same result: U = u - 1/2 and us = 1/2 - |U| are integer multiples of
+// 2^-53 (u = (2m+1) 2^-53), 2a doubles a positive number, and the floor, its
+// conversion and the comparisons of non-negative values use bit patterns.
+__device__ __forceinline__ long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+{
     const double slam = sqrt(lam);
     const double b = 0.931 + 2.53 * slam;
-    const double a = -0.059 + 0.02483 * b;
-    const double vr = 0.9277 - 3.6224 / (b - 2.0);
+    const double a = -0.059 + 0.02483 * b;                                      // > 0 for lam >= 10
+    const double two_a = __longlong_as_double(__double_as_longlong(a) + (1ll << 52));   // 2a, exactly
+    const double vr = 0.9277 - 3.6224 / (b - 2.0);                              // > 0 for lam >= 10
     // ln lam and 1/alpha serve only the acceptance test after the squeeze,
     // so they are formed on first use (same values, shorter common path)
     double loglam = 0.0, inv_alpha = 0.0;
     bool slow_ready = false;
     for (uint32_t it = 0; it < (uint32_t)kPtrsMaxIters; ++it) {
         const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
-        const double U = u01(w.x, w.y) - 0.5;
+        const unsigned long long n = 2 * (((((uint64_t)w.x) << 32) | (uint64_t)w.y) >> 12) + 1;   // u = n 2^-53
+        const long long dU = (long long)n - (1ll << 52);                                        // U = dU 2^-53
+        const unsigned long long aU = (unsigned long long)(dU < 0 ? -dU : dU);
+        const double U = dU < 0 ? -scaled53(aU) : scaled53(aU);
+        const double us = scaled53((1ull << 52) - aU);                                          // 1/2 - |U| > 0
         const double V = u01(w.z, w.w);
-        const double us = 0.5 - fabs(U);
-        const double kd = floor((2.0 * a / us + b) * U + lam + 0.43);
-        if (us >= 0.07 && V <= vr) return (kd > (double)kCountLimit) ? kCountLimit + 1 : (long long)kd;
-        if (kd < 0.0 || (us < 0.013 && V > us)) continue;
-        if (kd > (double)kCountLimit) return kCountLimit + 1;
+        const long long k = floor_to_ll((two_a / us + b) * U + lam + 0.43);
+        if (nn_ge(us, 0.07) && nn_ge(vr, V)) return (k > kCountLimit) ? kCountLimit + 1 : k;
+        if (k < 0 || (nn_gt(0.013, us) && nn_gt(V, us))) continue;
+        if (k > kCountLimit) return kCountLimit + 1;
         if (!slow_ready) {
             loglam = dlog(lam);
             inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
             slow_ready = true;
         }
+        const double kd = u53_to_double((unsigned long long)k);
         const double lhs = dlog(V * inv_alpha / (a / (us * us) + b));
-        const double rhs = -lam + kd * loglam - dlnfact((long long)kd);
-        if (lhs <= rhs) return (long long)kd;
+        const double rhs = -lam + kd * loglam - dlnfact(k);
+        if (lhs <= rhs) return k;
     }
     return -1;
+}
+
+// k ~ Poisson(lam) on the stream (sim, attempt, reaction j): 0 for lam <= 0,
+// kCountLimit + 1 for a mean at or above 2^40, inversion below 10, PTRS
+// from 10 on.
+__device__ __forceinline__ long long poisson(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                             uint32_t j, const double *__restrict__ inv)
+{
+    if (!(lam > 0.0)) return 0;
+    if (!(lam < 0x1p40)) return kCountLimit + 1;
+    if (lam < 10.0) return inversion_draw(lam, inversion_uniform(seed, sim, attempt, j), inv);
+    return ptrs_draw(lam, seed, sim, attempt, j);
 }
 
 }  // namespace f64

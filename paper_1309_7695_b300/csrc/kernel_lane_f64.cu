@@ -22,10 +22,21 @@ struct RefArith {
     }
     __device__ static __forceinline__ double neglog(double u) { return -f64::dlog(u); }
     __device__ static __forceinline__ double tau_of(double E, double a) { return E / a; }
-    __device__ static __forceinline__ long long poisson(double a, double tau, uint64_t seed, uint32_t sim,
-                                                        uint32_t attempt, uint32_t j, const double *inv)
+    __device__ static __forceinline__ double mean(double a, double tau) { return a * tau; }
+    __device__ static __forceinline__ bool inv_zero_sure(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                                         uint32_t j)
     {
-        return f64::poisson(a * tau, seed, sim, attempt, j, inv);
+        return f64::inversion_zero_sure(lam, f64::inversion_uniform(seed, sim, attempt, j));
+    }
+    __device__ static __forceinline__ long long inversion(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                                          uint32_t j, const double *inv)
+    {
+        return f64::inversion_draw(lam, f64::inversion_uniform(seed, sim, attempt, j), inv);
+    }
+    __device__ static __forceinline__ long long ptrs(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                                     uint32_t j)
+    {
+        return f64::ptrs_draw(lam, seed, sim, attempt, j);
     }
 };
 

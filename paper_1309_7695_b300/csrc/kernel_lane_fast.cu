@@ -1,6 +1,7 @@
 // Fast-mode instantiation of the lane-per-simulation kernel.
 //
-// FP32: propensities a_j, Poisson means a_j tau and the Poisson sampler,
+// FP32: propensities a_j, Poisson means a_j tau and the Poisson sampler
+// (inversion, and PTRS below means of 2^22 with an FP32 acceptance test),
 // -ln u and the event times E/a.  FP64: the simulated clock, the slot tree
 // (a0 and a0c as FP64 sums of the FP32 propensities), the critical test and
 // tau' (mu_i, sigma_i^2, the bounds and their minimum), as the reference
@@ -40,10 +41,21 @@ struct FastArith {
         return (double)(-logf((float)u));
     }
     __device__ static __forceinline__ double tau_of(double E, double a) { return (double)((float)E / (float)a); }
-    __device__ static __forceinline__ long long poisson(double a, double tau, uint64_t seed, uint32_t sim,
-                                                        uint32_t attempt, uint32_t j, const double *)
+    __device__ static __forceinline__ double mean(double a, double tau) { return (double)((float)a * (float)tau); }
+    __device__ static __forceinline__ bool inv_zero_sure(double, uint64_t, uint32_t, uint32_t, uint32_t)
     {
-        return fast::poisson((float)a * (float)tau, seed, sim, attempt, j);
+        return false;   // the FP32 inversion is cheap enough to run for every positive mean
+    }
+    __device__ static __forceinline__ long long inversion(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                                          uint32_t j, const double *)
+    {
+        return fast::inversion((float)lam, seed, sim, attempt, j);
+    }
+    __device__ static __forceinline__ long long ptrs(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                                     uint32_t j)
+    {
+        if (lam < (double)fast::kPtrsF32Limit) return fast::ptrs((float)lam, seed, sim, attempt, j);
+        return f64::ptrs_draw(lam, seed, sim, attempt, j);
     }
 };
 

@@ -356,9 +356,9 @@ __global__ void __launch_bounds__(256, 1) warp_f64_kernel(const SimArgs A)
     for (int i = threadIdx.x; i < A.L.words; i += blockDim.x) blob[i] = A.blob[i];
     const size_t model_bytes = model_smem_bytes(A.L);
     double *inv = reinterpret_cast<double *>(smem + model_bytes);
-    for (int k = threadIdx.x; k <= f64::kInversionCap; k += blockDim.x) inv[k] = k ? 1.0 / (double)k : 0.0;
+    for (int k = threadIdx.x; k < f64::kInvTable; k += blockDim.x) inv[k] = k ? 1.0 / (double)k : 0.0;
     __syncthreads();
-    const size_t inv_bytes = ((f64::kInversionCap + 1) * 8 + 15) & ~size_t(15);
+    const size_t inv_bytes = ((size_t)f64::kInvTable * 8 + 15) & ~size_t(15);
     unsigned char *mine = smem + model_bytes + inv_bytes + (size_t)warp * warp_workspace_bytes(A.L.N, A.L.M);
     const Workspace w = carve(mine, A.L.N, A.L.M);
     for (;;) {
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256, 1) warp_f64_kernel(const SimArgs A)
 
 size_t warp_f64_smem_bytes(const ModelLayout &L, int block_warps)
 {
-    const size_t inv_bytes = ((f64::kInversionCap + 1) * 8 + 15) & ~size_t(15);
+    const size_t inv_bytes = ((size_t)f64::kInvTable * 8 + 15) & ~size_t(15);
     return model_smem_bytes(L) + inv_bytes + (size_t)block_warps * warp_workspace_bytes(L.N, L.M);
 }
 

@@ -36,7 +36,10 @@
 //   uniforms(seed, sim, attempt, purpose, u_a, u_b)   two uniforms of a block
 //   neglog(u)                       -ln u
 //   tau_of(E, a)                    E / a (time to the next event)
-//   poisson(a, tau, seed, sim, attempt, j, inv)   k ~ Poisson(a tau)
+//   mean(a, tau)                    the Poisson mean a tau of a leap
+//   inv_zero_sure(lam, stream)      true only if inversion certainly gives 0
+//   inversion(lam, stream, inv)     k ~ Poisson(lam) for 0 < lam < 10
+//   ptrs(lam, stream)               k ~ Poisson(lam) for lam >= 10
 // Everything else -- the slot tree and its order, the critical set, tau',
 // the control flow and counters -- is shared and runs in FP64.
 #pragma once
@@ -51,7 +54,6 @@ namespace tl {
 namespace lane {
 
 constexpr int kStride = 33;
-constexpr int kBatch = 4;
 constexpr int kNodes = 63;
 enum : int { P_NEED = 0, P_TOP = 1, P_SSA = 2, P_DONE = 3, P_IDLE = 4 };
 
@@ -62,7 +64,7 @@ __host__ __device__ inline size_t r16(size_t v) { return (v + 15) & ~size_t(15);
 __host__ __device__ inline size_t lane_warp_bytes(int N, int M)
 {
     return r16(4 * (size_t)kStride * N) + r16(8 * (size_t)kStride * kNodes) + r16(8 * (size_t)M) +
-           r16(8 * (size_t)M) + r16(8 * (size_t)N) + r16((size_t)M) + r16((size_t)N);
+           r16(8 * (size_t)M) + r16(8 * (size_t)N) + r16((size_t)M) + r16((size_t)N) + r16(4 * (size_t)M);
 }
 
 struct LaneSmem {
@@ -73,6 +75,7 @@ struct LaneSmem {
     long long *xn;
     unsigned char *crit;
     unsigned char *irs;
+    unsigned short *jl;   // [2M] reactions queued for inversion ([0, M)) and PTRS ([M, 2M))
 };
 
 __device__ __forceinline__ LaneSmem carve_lane(unsigned char *p, int N, int M)
@@ -91,6 +94,8 @@ __device__ __forceinline__ LaneSmem carve_lane(unsigned char *p, int N, int M)
     w.crit = p;
     p += r16((size_t)M);
     w.irs = p;
+    p += r16((size_t)N);
+    w.jl = reinterpret_cast<unsigned short *>(p);
     return w;
 }
 
@@ -176,9 +181,9 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
         model_bytes = model_smem_bytes(A.L);
     }
     double *inv = reinterpret_cast<double *>(smem + model_bytes);
-    for (int k = threadIdx.x; k <= f64::kInversionCap; k += blockDim.x) inv[k] = k ? 1.0 / (double)k : 0.0;
+    for (int k = threadIdx.x; k < f64::kInvTable; k += blockDim.x) inv[k] = k ? 1.0 / (double)k : 0.0;
     __syncthreads();
-    const size_t inv_bytes = r16((f64::kInversionCap + 1) * 8);
+    const size_t inv_bytes = r16((size_t)f64::kInvTable * 8);
     const int wN = kMulti ? A.max_N : A.L.N, wM = kMulti ? A.max_M : A.L.M;
     const LaneSmem w = carve_lane(smem + model_bytes + inv_bytes + (size_t)warp * lane_warp_bytes(wN, wM), wN, wM);
     int *const X = w.X;
@@ -203,10 +208,6 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
     int first = 0;
     long long leaps = 0, rejected = 0, ssa_steps = 0, firings = 0;
     double tnext = kInf;   // T[ks], or +inf once every sample is recorded
-    // batched SSA draws: -ln u1 and u2 for attempts eb_att .. eb_att + kBatch - 1
-    bool eb_valid = false;
-    uint32_t eb_att = 0;
-    double eb_E[kBatch], eb_U[kBatch];
 
     auto own_prop = [&](const GroupView &G, int j) -> double {
         return Arith::prop(G.rinfo[j], __ldg(G.params + (size_t)row * G.M + j), X, kStride, lane);
@@ -255,7 +256,6 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     attempt = 0;
                     status = SSA_STATUS_OK;
                     leaps = rejected = ssa_steps = firings = 0;
-                    eb_valid = false;
                     tnext = (S > 0) ? T[0] : kInf;
                     for (int i = 0; i < N; ++i) X[i * kStride + lane] = G.x0[(size_t)row * N + i];
                     if (exact) lane_build_tree(G);
@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     }
                     double Lv[6];
                     const double a0 = slot_tree(s, Lv);
+                    const double ssa_thr = A.ssa_factor / a0;   // the SSA-fallback threshold
 #pragma unroll
                     for (int k = 0; k <= 5; ++k)
                         if (lane < (32 >> k)) V[(node_base(k) + lane) * kStride + L] = Lv[k];
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 }
                             }
                             const double a = w.a[j];
-                            const bool cr = (a > 0.0) && (Lj < (long long)A.n_c);
+                            const bool cr = f64::nn_pos(a) && (Lj < (long long)A.n_c);
                             w.crit[j] = cr;
                             sc = sc + (cr ? a : 0.0);
                         }
@@ -367,26 +368,28 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 const int j = ent >> 8;
                                 if (w.crit[j]) continue;
                                 const double a = w.a[j];
-                                if (!(a > 0.0)) continue;
+                                if (!f64::nn_pos(a)) continue;
                                 const int nv = (signed char)(ent & 0xff);
-                                mu = mu + (double)nv * a;
-                                sig2 = sig2 + (double)(nv * nv) * a;
+                                mu = mu + f64::small_to_double(nv) * a;
+                                sig2 = sig2 + f64::count_to_double(nv * nv) * a;
                             }
                             const int xi = X[i * kStride + L];
-                            const double xd = (double)xi;
-                            double g;
+                            const double xd = f64::count_to_double(xi);
+                            // bound = (eps x_i) / g_i; dividing by g = 1 or 2 is exact, so
+                            // those cases multiply (same value, no division)
                             const int h = hor[i];
-                            if (h == 1) g = 1.0;
-                            else if (h == 2) g = 2.0;
-                            else g = (xi >= 2) ? 2.0 + 1.0 / (xd - 1.0) : 2.0;
-                            double bound = (A.eps * xd) / g;
-                            if (bound < 1.0) bound = 1.0;
-                            if (mu != 0.0) {
+                            const double ex = A.eps * xd;
+                            double bound;
+                            if (h == 1) bound = ex;
+                            else if (h == 2 || xi < 2) bound = ex * 0.5;
+                            else bound = ex / (2.0 + 1.0 / (xd - 1.0));
+                            if (f64::dbits(bound) < f64::dbits(1.0)) bound = 1.0;
+                            if ((f64::dbits(mu) << 1) != 0) {   // mu != 0
                                 const unsigned long long b1 =
                                     (unsigned long long)__double_as_longlong(bound / fabs(mu));
                                 tmin = b1 < tmin ? b1 : tmin;
                             }
-                            if (sig2 != 0.0) {
+                            if (f64::nn_pos(sig2)) {   // sig2 >= 0; != 0
                                 const unsigned long long b2 =
                                     (unsigned long long)__double_as_longlong((bound * bound) / sig2);
                                 tmin = b2 < tmin ? b2 : tmin;
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 
                         int halvings = 0;
                         for (;;) {
-                            if (tau1 < A.ssa_factor / a0) {
+                            if (tau1 < ssa_thr) {
                                 nphase = P_SSA;
                                 nleft = A.ssa_block;
                                 nfirst = 1;
@@ -410,32 +413,79 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             attL = attL + 1;
                             double u_tau, u_sel;
                             Arith::uniforms(GL.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
-                            const double tau2 = (a0c > 0.0) ? Arith::tau_of(Arith::neglog(u_tau), a0c) : kInf;
+                            const double tau2 = f64::nn_pos(a0c) ? Arith::tau_of(Arith::neglog(u_tau), a0c) : kInf;
                             const double t_stop = (ksL < S) ? tnL : t_end;
                             const double delta = t_stop - tL;
                             double tau;
                             int jc = -1;
                             bool clamp = false;
-                            if (tau2 <= tau1 && tau2 <= delta) {
+                            // tau2, tau1 and delta are positive (or +inf): compare bit patterns
+                            if (f64::nn_ge(tau1, tau2) && f64::nn_ge(delta, tau2)) {
                                 tau = tau2;
                                 jc = slot_select(Lc, u_sel * a0c, w.a, w.crit, true, M);
-                            } else if (delta <= tau1) {
+                            } else if (f64::nn_ge(tau1, delta)) {
                                 tau = delta;
                                 clamp = true;
                             } else {
                                 tau = tau1;
                             }
+                            // Poisson counts of the noncritical reactions.  A first pass
+                            // forms the means and settles the trivial draws (critical
+                            // reactions, zero means, certain zeros); the rest are queued by
+                            // sampler and drawn in two compacted passes, so a warp runs each
+                            // sampler once per 32 queued draws instead of branching over
+                            // both for every reaction.  Each draw depends only on its own
+                            // mean and stream, so the order is free.
                             int krej = 0, kover = 0;
                             long long ksum = 0;
-                            for (int j = lane; j < M; j += 32) {
-                                long long kj;
-                                if (w.crit[j]) {
-                                    kj = (j == jc) ? 1 : 0;
-                                } else {
-                                    kj = Arith::poisson(w.a[j], tau, GL.seed, sL, attL, (uint32_t)j, inv);
-                                    if (kj < 0) krej = 1;
-                                    else if (kj > f64::kCountLimit) kover = 1;
+                            int n_inv = 0, n_ptrs = 0;
+                            const unsigned lt = (1u << lane) - 1u;
+                            for (int j0 = 0; j0 < M; j0 += 32) {
+                                const int j = j0 + lane;
+                                int cls = 0;   // 0 settled, 1 inversion, 2 PTRS
+                                if (j < M) {
+                                    long long kj = 0;
+                                    if (w.crit[j]) {
+                                        kj = (j == jc) ? 1 : 0;
+                                    } else {
+                                        // a_j >= 0 and tau is finite and positive, so lam is a
+                                        // finite non-negative double and compares by its bits
+                                        const double lam = Arith::mean(w.a[j], tau);
+                                        if (f64::nn_pos(lam)) {
+                                            if (f64::dbits(lam) >= f64::dbits(0x1p40)) {
+                                                kj = f64::kCountLimit + 1;
+                                                kover = 1;
+                                            } else if (f64::dbits(lam) < f64::dbits(10.0)) {
+                                                if (!Arith::inv_zero_sure(lam, GL.seed, sL, attL, (uint32_t)j)) cls = 1;
+                                            } else {
+                                                cls = 2;
+                                            }
+                                            if (cls) kj = __double_as_longlong(lam);   // mean parked until drawn
+                                        }
+                                    }
+                                    w.k[j] = kj;
+                                    if (!cls) ksum += kj;
                                 }
+                                const unsigned bi = __ballot_sync(kFull, cls == 1);
+                                const unsigned bp = __ballot_sync(kFull, cls == 2);
+                                if (cls == 1) w.jl[n_inv + __popc(bi & lt)] = (unsigned short)j;
+                                if (cls == 2) w.jl[M + n_ptrs + __popc(bp & lt)] = (unsigned short)j;
+                                n_inv += __popc(bi);
+                                n_ptrs += __popc(bp);
+                            }
+                            __syncwarp();
+                            for (int q = lane; q < n_inv; q += 32) {
+                                const int j = w.jl[q];
+                                const long long kj =
+                                    Arith::inversion(__longlong_as_double(w.k[j]), GL.seed, sL, attL, (uint32_t)j, inv);
+                                w.k[j] = kj;
+                                ksum += kj;
+                            }
+                            for (int q = lane; q < n_ptrs; q += 32) {
+                                const int j = w.jl[M + q];
+                                const long long kj = Arith::ptrs(__longlong_as_double(w.k[j]), GL.seed, sL, attL, (uint32_t)j);
+                                if (kj < 0) krej = 1;
+                                else if (kj > f64::kCountLimit) kover = 1;
                                 w.k[j] = kj;
                                 ksum += kj;
                             }
@@ -556,26 +606,13 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     phase = P_DONE;
                 } else {
                     attempt = attempt + 1;
-                    // -ln u1 and u2 of this attempt; the next kBatch attempts are drawn
-                    // together so their log chains overlap (same values as one by one)
-                    if (!(eb_valid && attempt - eb_att < (uint32_t)kBatch)) {
-                        eb_att = attempt;
-                        eb_valid = true;
-#pragma unroll
-                        for (int q = 0; q < kBatch; ++q) {
-                            double u1;
-                            Arith::uniforms(G.seed, sim, attempt + q, PURPOSE_SSA, u1, eb_U[q]);
-                            eb_E[q] = Arith::neglog(u1);
-                        }
-                    }
-                    const uint32_t pos = attempt - eb_att;
-                    double E = eb_E[0], u2 = eb_U[0];
-#pragma unroll
-                    for (int q = 1; q < kBatch; ++q)
-                        if (pos == (uint32_t)q) {
-                            E = eb_E[q];
-                            u2 = eb_U[q];
-                        }
+                    // -ln u1 and u2 of this attempt.  Every lane in this phase draws in
+                    // the same iteration, so the FP64 work of the logarithm is one
+                    // converged pass for the whole warp (an FP64 instruction costs the
+                    // same however many lanes are active).
+                    double u1, u2;
+                    Arith::uniforms(G.seed, sim, attempt, PURPOSE_SSA, u1, u2);
+                    const double E = Arith::neglog(u1);
                     const double tau = Arith::tau_of(E, a0);
                     const double t_new = t + tau;
                     while (ks < S && !f64::nn_ge(tnext, t_new)) {
@@ -692,12 +729,12 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
 
 inline size_t lane_smem_bytes(const ModelLayout &L, int block_warps)
 {
-    return model_smem_bytes(L) + lane::r16((f64::kInversionCap + 1) * 8) + (size_t)block_warps * lane::lane_warp_bytes(L.N, L.M);
+    return model_smem_bytes(L) + lane::r16((size_t)f64::kInvTable * 8) + (size_t)block_warps * lane::lane_warp_bytes(L.N, L.M);
 }
 
 inline size_t lane_multi_bytes(int max_N, int max_M, int block_warps)
 {
-    return lane::r16((f64::kInversionCap + 1) * 8) + (size_t)block_warps * lane::lane_warp_bytes(max_N, max_M);
+    return lane::r16((size_t)f64::kInvTable * 8) + (size_t)block_warps * lane::lane_warp_bytes(max_N, max_M);
 }
 
 template <class Arith, bool kMulti>

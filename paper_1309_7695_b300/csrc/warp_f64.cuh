@@ -23,6 +23,8 @@ __device__ __forceinline__ double slot_tree(double v, double L[6])
 // slot tree (second child when target >= first child and second child > 0),
 // then walk the chosen slot's reactions in increasing j.  When `crit_only`
 // the weights are the critical propensities (0 for noncritical reactions).
+// All weights, sums and the target are non-negative, so the comparisons run
+// on their bit patterns.
 __device__ __forceinline__ int slot_select(const double L[6], double target, const double *a,
                                            const unsigned char *crit, bool crit_only, int M)
 {
@@ -32,7 +34,7 @@ __device__ __forceinline__ int slot_select(const double L[6], double target, con
         const int step = 1 << (4 - k);
         const double left = __shfl_sync(kFull, L[k], cls);
         const double right = __shfl_sync(kFull, L[k], cls + step);
-        if (target >= left && right > 0.0) {
+        if (f64::nn_ge(target, left) && f64::nn_pos(right)) {
             target = target - left;
             cls += step;
         }
@@ -42,8 +44,8 @@ __device__ __forceinline__ int slot_select(const double L[6], double target, con
     for (int j = cls; j < M; j += 32) {
         const double v = (crit_only && !crit[j]) ? 0.0 : a[j];
         cum = cum + v;
-        if (v > 0.0) last = j;
-        if (cum > target) return j;
+        if (f64::nn_pos(v)) last = j;
+        if (f64::nn_gt(cum, target)) return j;
     }
     return last;
 }
