@@ -29,9 +29,11 @@
  *  - Poisson variates: inversion by sequential search for small means and
  *    the transformed-rejection method PTRS (Hormann 1993, Insurance: Math.
  *    and Economics 12) for means >= 10.
- *  - log / exp / log k!: self-contained functions built from +,-,*,/ only
- *    (atanh series for log, Cody-Waite reduction + Taylor polynomial for
- *    exp, Stirling series for log k!), so no platform libm enters a result.
+ *  - log / exp / log k!: self-contained functions built from +,-,*,/ and
+ *    fma only (Tang's table method for log, its table summed from the atanh
+ *    series in double-double arithmetic; Cody-Waite reduction + Taylor
+ *    polynomial for exp; Stirling series for log k!), so no platform libm
+ *    enters a result.
  *
  * Pinning: see tests/test_oracle_*.py (closed forms, exact CME solutions,
  * libm ulp bounds, Poisson pmf, Philox known-answer values, invariants).
@@ -124,14 +126,101 @@ double oracle_u01(uint32_t w0, uint32_t w1)
 static const double LN2_HI = 0x1.62e42feep-1;
 static const double LN2_LO = 0x1.a39ef35793c76p-33;
 static const double INV_LN2 = 0x1.71547652b82fep+0;   /* 1/ln 2 rounded */
-static const double SQRT2 = 0x1.6a09e667f3bcdp+0;     /* sqrt(2) rounded */
 static const double HALF_LN_2PI = 0x1.d67f1c864beb5p-1; /* ln(2 pi)/2 rounded */
 
-/* Natural log of a finite x > 0.
- * x = 2^e * m with m in [sqrt(2)/2, sqrt(2)]; ln m = 2 atanh(s),
- * s = (m-1)/(m+1), atanh(s)/s = sum_{n>=0} s^(2n)/(2n+1) truncated after
- * the s^20 term (|s| <= 0.1716, so the first omitted term is < 1e-18
- * relative). */
+/* ---- table of the logarithm (built once, in double-double arithmetic) ----
+ * For j = 0..256 the grid point F_j = 1 + j/256 (exact).  LOG_INV[j] =
+ * RN(1/F_j).  (LOG_HI[j], LOG_LO[j]) is ln F_j for F_j <= sqrt 2 (j <= 106)
+ * and ln(F_j / 2) above, as an unevaluated sum of two doubles.  The pair is
+ * computed by the atanh series ln y = 2 atanh(s), s = (y-1)/(y+1), summed in
+ * double-double arithmetic (Dekker's exact products via fma, Knuth's exact
+ * sums) to about 2^-104; the engine builds its own copy by the same
+ * sequence of operations, so the two tables agree bit for bit. */
+typedef struct { double hi, lo; } dd_t;
+
+static dd_t dd_two_sum(double a, double b)
+{
+    dd_t r;
+    r.hi = a + b;
+    double bb = r.hi - a;
+    r.lo = (a - (r.hi - bb)) + (b - bb);
+    return r;
+}
+
+static dd_t dd_fast_two_sum(double a, double b)   /* |a| >= |b| or a = 0 */
+{
+    dd_t r;
+    r.hi = a + b;
+    r.lo = b - (r.hi - a);
+    return r;
+}
+
+static dd_t dd_add(dd_t x, dd_t y)
+{
+    dd_t s = dd_two_sum(x.hi, y.hi);
+    dd_t t = dd_two_sum(x.lo, y.lo);
+    s.lo = s.lo + t.hi;
+    s = dd_fast_two_sum(s.hi, s.lo);
+    s.lo = s.lo + t.lo;
+    return dd_fast_two_sum(s.hi, s.lo);
+}
+
+static dd_t dd_mul(dd_t x, dd_t y)
+{
+    double p = x.hi * y.hi;
+    double e = fma(x.hi, y.hi, -p);
+    e = e + (x.hi * y.lo + x.lo * y.hi);
+    return dd_fast_two_sum(p, e);
+}
+
+/* a / b for doubles, to double-double: RN quotient plus the exact remainder
+ * divided by b. */
+static dd_t dd_div_d(double a, double b)
+{
+    dd_t q;
+    q.hi = a / b;
+    q.lo = fma(-q.hi, b, a) / b;
+    return q;
+}
+
+#define LOG_TABLE_N 257
+#define LOG_SERIES_TERMS 36 /* |s| <= 1/3: the first omitted term is below 2^-115 */
+static double LOG_INV[LOG_TABLE_N], LOG_HI[LOG_TABLE_N], LOG_LO[LOG_TABLE_N];
+
+static void build_log_table(void)
+{
+    for (int j = 0; j < LOG_TABLE_N; ++j) {
+        double F = 1.0 + (double)j * 0x1p-8;
+        LOG_INV[j] = 1.0 / F;
+        double y = (j <= 106) ? F : F * 0.5;
+        dd_t s = dd_div_d(y - 1.0, y + 1.0);
+        dd_t z = dd_mul(s, s);
+        /* atanh(s)/s = sum_k z^k / (2k+1), Horner from the last term */
+        dd_t acc = dd_div_d(1.0, (double)(2 * LOG_SERIES_TERMS + 1));
+        for (int k = LOG_SERIES_TERMS - 1; k >= 0; --k)
+            acc = dd_add(dd_mul(acc, z), dd_div_d(1.0, (double)(2 * k + 1)));
+        dd_t r = dd_mul(s, acc);
+        r.hi = 2.0 * r.hi;   /* exact */
+        r.lo = 2.0 * r.lo;
+        dd_t n = dd_fast_two_sum(r.hi, r.lo);
+        LOG_HI[j] = n.hi;
+        LOG_LO[j] = n.lo;
+    }
+}
+
+/* built when the library is loaded, before any caller can use oracle_log */
+__attribute__((constructor)) static void oracle_init_tables(void) { build_log_table(); }
+
+/* Natural log of a finite x > 0 (Tang's table method, written from the
+ * mathematics).  x = 2^e m with m in [1, 2); F = 1 + j/256 is the grid
+ * point nearest m, and f = m - F is exact with |f| <= 2^-9.  Then
+ *   ln x = e ln 2 + ln F + ln(1 + r),  r = f * RN(1/F),
+ * where, for F > sqrt 2, ln F is replaced by ln(F/2) and e by e + 1 so that
+ * x near 1 from either side meets the table entry ln 1 = 0 (no
+ * cancellation).  ln(1 + r) = r + r^2 (-1/2 + r/3 - r^2/4 + r^3/5 - r^4/6);
+ * the first omitted term is below 2^-56 relative for |r| <= 2^-9.  The
+ * exact product e * LN2_HI and the table's high part are added with their
+ * rounding error kept (Fast2Sum), the low parts and ln(1 + r) after. */
 double oracle_log(double x)
 {
     uint64_t bits;
@@ -145,29 +234,27 @@ double oracle_log(double x)
         adj = -54;
     }
     int e = biased - 1023 + adj;
-    bits = (bits & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
+    uint64_t mant = bits & 0x000fffffffffffffULL;
+    int j = (int)((mant + (1ULL << 43)) >> 44);   /* nearest 1/256 step, 0..256 */
+    uint64_t mb = mant | 0x3ff0000000000000ULL;
     double m;
-    memcpy(&m, &bits, sizeof m);  /* m in [1, 2) */
-    if (m > SQRT2) {
-        m = m * 0.5;
-        e = e + 1;
-    }
-    double s = (m - 1.0) / (m + 1.0);
-    double z = s * s;
-    double p = 1.0 / 21.0;
-    p = p * z + 1.0 / 19.0;
-    p = p * z + 1.0 / 17.0;
-    p = p * z + 1.0 / 15.0;
-    p = p * z + 1.0 / 13.0;
-    p = p * z + 1.0 / 11.0;
-    p = p * z + 1.0 / 9.0;
-    p = p * z + 1.0 / 7.0;
-    p = p * z + 1.0 / 5.0;
-    p = p * z + 1.0 / 3.0;
-    double two_s = 2.0 * s;
-    double lm = two_s + two_s * (z * p);
+    memcpy(&m, &mb, sizeof m);                    /* m in [1, 2) */
+    double F = 1.0 + (double)j * 0x1p-8;          /* exact */
+    if (j > 106) e = e + 1;
+    double f = m - F;                             /* exact */
+    double r = f * LOG_INV[j];
+    double p = -1.0 / 6.0;
+    p = p * r + 1.0 / 5.0;
+    p = p * r - 1.0 / 4.0;
+    p = p * r + 1.0 / 3.0;
+    p = p * r - 1.0 / 2.0;
+    double q = r + (r * r) * p;
     double de = (double)e;
-    return de * LN2_HI + (lm + de * LN2_LO);
+    double a = de * LN2_HI;                       /* exact */
+    double hi = a + LOG_HI[j];
+    double err = LOG_HI[j] - (hi - a);            /* |a| >= |LOG_HI| or a = 0 */
+    double lo = ((de * LN2_LO + LOG_LO[j]) + err) + q;
+    return hi + lo;
 }
 
 /* e^x.  x = n ln2 + r with n = floor(x/ln2 + 1/2) and |r| <= ln2/2

@@ -9,6 +9,8 @@
 
 #include <stdint.h>
 
+#include <mutex>
+
 #include "engine.h"
 
 namespace tl {
@@ -90,12 +92,112 @@ __device__ __forceinline__ double small_to_double(int v)
 #define TL_LN2_HI 0x1.62e42feep-1
 #define TL_LN2_LO 0x1.a39ef35793c76p-33
 #define TL_INV_LN2 0x1.71547652b82fep+0
-#define TL_SQRT2 0x1.6a09e667f3bcdp+0
 #define TL_HALF_LN_2PI 0x1.d67f1c864beb5p-1
 
-// ln x for finite x > 0: x = 2^e m, m in [sqrt2/2, sqrt2]; ln m = 2 atanh(s)
-// with s = (m-1)/(m+1) and atanh(s)/s = sum_n s^(2n)/(2n+1), kept through
-// the s^20 term, evaluated in Horner form in z = s^2.
+// ---- logarithm table, built on the host in double-double arithmetic ----
+// Entry j = 0..256 belongs to the grid point F_j = 1 + j/256:
+//   inv[j] = RN(1/F_j),
+//   (hi[j], lo[j]) = ln F_j for j <= 106 (F_j <= sqrt 2), ln(F_j / 2) above,
+// the latter from ln y = 2 atanh(s), s = (y-1)/(y+1), with the series
+// summed in double-double arithmetic (exact products by fma, exact sums by
+// Knuth's and Dekker's two-sum) to about 2^-104.  The values are a fixed
+// function of this sequence of IEEE operations.
+constexpr int kLogTableN = 257;
+constexpr int kLogSeriesTerms = 36;   // |s| <= 1/3: first omitted term below 2^-115
+
+namespace logtab {
+struct DD {
+    double hi, lo;
+};
+inline DD two_sum(double a, double b)
+{
+    const double s = a + b;
+    const double bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+inline DD fast_two_sum(double a, double b)   // |a| >= |b| or a == 0
+{
+    const double s = a + b;
+    return {s, b - (s - a)};
+}
+inline DD add(DD x, DD y)
+{
+    DD s = two_sum(x.hi, y.hi);
+    const DD t = two_sum(x.lo, y.lo);
+    s.lo = s.lo + t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = s.lo + t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+inline DD mul(DD x, DD y)
+{
+    const double p = x.hi * y.hi;
+    double e = fma(x.hi, y.hi, -p);
+    e = e + (x.hi * y.lo + x.lo * y.hi);
+    return fast_two_sum(p, e);
+}
+inline DD div_d(double a, double b)   // RN(a/b) and the exact remainder over b
+{
+    const double q = a / b;
+    return {q, fma(-q, b, a) / b};
+}
+// tab[0..257) = inv, tab[257..514) = hi, tab[514..771) = lo
+inline void build(double *tab)
+{
+    for (int j = 0; j < kLogTableN; ++j) {
+        const double F = 1.0 + (double)j * 0x1p-8;
+        tab[j] = 1.0 / F;
+        const double y = (j <= 106) ? F : F * 0.5;
+        const DD sv = div_d(y - 1.0, y + 1.0);
+        const DD z = mul(sv, sv);
+        DD acc = div_d(1.0, (double)(2 * kLogSeriesTerms + 1));
+        for (int k = kLogSeriesTerms - 1; k >= 0; --k) acc = add(mul(acc, z), div_d(1.0, (double)(2 * k + 1)));
+        DD r = mul(sv, acc);
+        r.hi = 2.0 * r.hi;
+        r.lo = 2.0 * r.lo;
+        const DD n = fast_two_sum(r.hi, r.lo);
+        tab[kLogTableN + j] = n.hi;
+        tab[2 * kLogTableN + j] = n.lo;
+    }
+}
+}  // namespace logtab
+
+// This translation unit's device copy of the table (without relocatable
+// device code every unit that evaluates dlog holds its own).
+static __device__ double g_log_tab[3 * kLogTableN];
+
+// Upload this unit's table to the current device, once per device (the
+// first launch on a device does it; it allocates nothing).
+static inline cudaError_t ensure_log_table()
+{
+    static std::mutex mu;
+    static bool built = false, done[256] = {false};
+    static double host[3 * kLogTableN];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    if (!built) {
+        logtab::build(host);
+        built = true;
+    }
+    e = cudaMemcpyToSymbol(g_log_tab, host, sizeof host);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+// ln x for finite x > 0 (Tang's table method, written from the
+// mathematics).  x = 2^e m, m in [1, 2); F = 1 + j/256 is the grid point
+// nearest m and f = m - F is exact, |f| <= 2^-9.  Then
+//   ln x = e ln 2 + ln F + ln(1 + r),  r = f RN(1/F),
+// with ln(F/2) and e + 1 in place of ln F and e when F > sqrt 2, so that x
+// near 1 from either side meets the entry ln 1 = 0.  ln(1 + r) = r + r^2
+// (-1/2 + r/3 - r^2/4 + r^3/5 - r^4/6), first omitted term below 2^-56
+// relative.  e LN2_HI is exact; its sum with the table's high part keeps its
+// rounding error (Fast2Sum), and the low parts and ln(1 + r) are added after.
+// F and e as doubles are assembled from bits (exact, off the FP64 unit).
 __device__ __forceinline__ double dlog(double x)
 {
     long long bits = __double_as_longlong(x);
@@ -108,27 +210,27 @@ __device__ __forceinline__ double dlog(double x)
         adj = -54;
     }
     int e = biased - 1023 + adj;
-    double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
-    if (m > TL_SQRT2) {
-        m = m * 0.5;
-        e = e + 1;
-    }
-    const double s = (m - 1.0) / (m + 1.0);
-    const double z = s * s;
-    double p = 1.0 / 21.0;
-    p = p * z + 1.0 / 19.0;
-    p = p * z + 1.0 / 17.0;
-    p = p * z + 1.0 / 15.0;
-    p = p * z + 1.0 / 13.0;
-    p = p * z + 1.0 / 11.0;
-    p = p * z + 1.0 / 9.0;
-    p = p * z + 1.0 / 7.0;
-    p = p * z + 1.0 / 5.0;
-    p = p * z + 1.0 / 3.0;
-    const double two_s = 2.0 * s;
-    const double lm = two_s + two_s * (z * p);
-    const double de = (double)e;
-    return de * TL_LN2_HI + (lm + de * TL_LN2_LO);
+    const unsigned long long mant = (unsigned long long)bits & 0x000FFFFFFFFFFFFFull;
+    const int j = (int)((mant + (1ull << 43)) >> 44);   // nearest 1/256 step, 0..256
+    const double m = __longlong_as_double((long long)(mant | 0x3FF0000000000000ull));
+    const double F = __longlong_as_double(j < 256 ? (long long)(0x3FF0000000000000ull | ((unsigned long long)j << 44))
+                                                  : (long long)0x4000000000000000ull);
+    if (j > 106) e = e + 1;
+    const double f = m - F;
+    const double r = f * __ldg(&g_log_tab[j]);
+    double p = -1.0 / 6.0;
+    p = p * r + 1.0 / 5.0;
+    p = p * r - 1.0 / 4.0;
+    p = p * r + 1.0 / 3.0;
+    p = p * r - 1.0 / 2.0;
+    const double q = r + (r * r) * p;
+    const double de = small_to_double(e);
+    const double a = de * TL_LN2_HI;
+    const double ghi = __ldg(&g_log_tab[kLogTableN + j]);
+    const double hi = a + ghi;
+    const double err = ghi - (hi - a);
+    const double lo = ((de * TL_LN2_LO + __ldg(&g_log_tab[2 * kLogTableN + j])) + err) + q;
+    return hi + lo;
 }
 
 // e^x: n = floor(x/ln2 + 1/2), r = (x - n LN2_HI) - n LN2_LO, e^r by the

@@ -12,6 +12,37 @@
 namespace tl {
 namespace fast {
 
+// Conversions between FP32 and FP64 assembled from bits on the integer pipe
+// (on this GPU a conversion instruction costs as much as an FP64 add).
+// Both give the IEEE result: float -> double is exact, double -> float
+// rounds to nearest even.  Values outside the normal float range (zero
+// aside) take the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if ((u << 1) == 0) return __longlong_as_double((long long)sign);   // +-0
+    if (e == 0 || e == 255) return (double)f;
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + (1023 - 127)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+__device__ __forceinline__ float f64_to_f32(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    if ((b << 1) == 0) return __uint_as_float(sign);   // +-0
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -126 || e > 127) return __double2float_rn(d);
+    const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
+    const unsigned m23 = (unsigned)(mant >> 29);
+    const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
+    unsigned r = ((unsigned)(e + 127) << 23) | m23;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) r += 1;   // a carry moves into the exponent
+    return __uint_as_float(sign | r);
+}
+
 // Uniform in (0,1) from the top 23 bits of one word: ((w >> 9) + 1/2) 2^-23.
 // It takes the leading bits of the reference mode's 52-bit uniform.
 __device__ __forceinline__ float u23(uint32_t w) { return ((float)(w >> 9) + 0.5f) * 0x1p-23f; }
@@ -94,10 +125,10 @@ __device__ __forceinline__ long long ptrs(float lam, uint64_t seed, uint32_t sim
         const float V = u23(w.z);
         const float us = 0.5f - fabsf(U);
         const float kf = floorf((__fdividef(2.0f * a, us) + b) * U + lam + 0.43f);
-        if (us >= 0.07f && V <= vr) return (long long)kf;
+        if (us >= 0.07f && V <= vr) return (long long)__float2int_rz(kf);   // kf >= 0 here for lam >= 10
         if (kf < 0.0f || (us < 0.013f && V > us)) continue;
         const float lhs = __logf(V * inv_alpha / (a / (us * us) + b));
-        if (lhs <= log_pmf(kf, lam)) return (long long)kf;
+        if (lhs <= log_pmf(kf, lam)) return (long long)__float2int_rz(kf);
     }
     return -1;
 }

@@ -740,8 +740,9 @@ inline size_t lane_multi_bytes(int max_N, int max_M, int block_warps)
 template <class Arith, bool kMulti>
 cudaError_t launch_lane_impl(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = f64::ensure_log_table();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     lane::lane_kernel<Arith, kMulti><<<grid, block_warps * 32, smem, s>>>(a);
     return cudaGetLastError();
