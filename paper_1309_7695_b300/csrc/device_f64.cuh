@@ -79,6 +79,15 @@ __device__ __forceinline__ double u53_to_double(unsigned long long v)
     return __longlong_as_double((long long)(((unsigned long long)(1023 + p) << 52) | frac));
 }
 __device__ __forceinline__ double count_to_double(int x) { return u53_to_double((unsigned long long)(unsigned)x); }
+// +0 + a for a propensity a (>= +0, or -0 from a -0 rate): the canonical
+// sums start from +0, and adding the first term to +0 only clears the sign
+// of a zero, so the first term is taken with its sign bit cleared (integer
+// pipe) instead of being added.
+__device__ __forceinline__ double first_term(double a)
+{
+    return __longlong_as_double(__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll);
+}
+
 // Exact conversion of a small signed integer (|v| < 2^31), from bits.
 __device__ __forceinline__ double small_to_double(int v)
 {

@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
     };
     auto lane_build_tree = [&](const GroupView &G) {
         for (int l = 0; l < 32; ++l) {
-            double s = 0.0;
-            for (int j = l; j < G.M; j += 32) s = s + own_prop(G, j);
+            double s = (l < G.M) ? f64::first_term(own_prop(G, l)) : 0.0;
+            for (int j = l + 32; j < G.M; j += 32) s = s + own_prop(G, j);
             V[l * kStride + lane] = s;
         }
         for (int k = 1; k <= 5; ++k) {
@@ -308,7 +308,12 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     nphase = P_DONE;
                 } else {
                     double s = 0.0;
-                    for (int j = lane; j < M; j += 32) {
+                    if (lane < M) {   // first term of the slot sum (no add to +0)
+                        const double a = Arith::prop(rinfo[lane], cL[lane], X, kStride, L);
+                        w.a[lane] = a;
+                        s = f64::first_term(a);
+                    }
+                    for (int j = lane + 32; j < M; j += 32) {
                         const double a = Arith::prop(rinfo[j], cL[j], X, kStride, L);
                         w.a[j] = a;
                         s = s + a;
@@ -329,6 +334,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     } else {
                         // critical set (CGP 2005) and a0c
                         double sc = 0.0;
+                        bool sc_started = false;   // the first critical term is taken, not added to +0
                         for (int j = lane; j < M; j += 32) {
                             long long Lj = LLONG_MAX;
                             for (int e = nu_ptr[j]; e < nu_ptr[j + 1]; ++e) {
@@ -344,7 +350,11 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             const double a = w.a[j];
                             const bool cr = f64::nn_pos(a) && (Lj < (long long)A.n_c);
                             w.crit[j] = cr;
-                            sc = sc + (cr ? a : 0.0);
+                            if (cr) {
+                                if (sc_started) sc = sc + a;
+                                else sc = a;   // a > 0
+                                sc_started = true;
+                            }
                         }
                         for (int i = lane; i < N; i += 32) w.irs[i] = 0;
                         __syncwarp();
@@ -640,7 +650,8 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         int jf = -1, last = -1;
                         for (int j = cls; j < M; j += 32) {
                             const double v = own_prop(G, j);
-                            cum = cum + v;
+                            if (j == cls) cum = f64::first_term(v);
+                            else cum = cum + v;
                             if (f64::nn_pos(v)) last = j;
                             if (f64::nn_gt(cum, target)) {
                                 jf = j;
@@ -674,8 +685,8 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 while (m) {
                                     const int l = __ffs(m) - 1;
                                     m &= m - 1;
-                                    double s = 0.0;
-                                    for (int j = l; j < M; j += 32) s = s + own_prop(G, j);
+                                    double s = f64::first_term(own_prop(G, l));   // l < M: a dirty slot holds a reaction
+                                    for (int j = l + 32; j < M; j += 32) s = s + own_prop(G, j);
                                     V[l * kStride + lane] = s;
                                 }
 #pragma unroll

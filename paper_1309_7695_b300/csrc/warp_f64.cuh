@@ -43,7 +43,8 @@ __device__ __forceinline__ int slot_select(const double L[6], double target, con
     int last = -1;
     for (int j = cls; j < M; j += 32) {
         const double v = (crit_only && !crit[j]) ? 0.0 : a[j];
-        cum = cum + v;
+        if (j == cls) cum = f64::first_term(v);
+        else cum = cum + v;
         if (f64::nn_pos(v)) last = j;
         if (f64::nn_gt(cum, target)) return j;
     }
