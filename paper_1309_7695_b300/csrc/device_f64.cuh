@@ -79,6 +79,37 @@ __device__ __forceinline__ double u53_to_double(unsigned long long v)
     return __longlong_as_double((long long)(((unsigned long long)(1023 + p) << 52) | frac));
 }
 __device__ __forceinline__ double count_to_double(int x) { return u53_to_double((unsigned long long)(unsigned)x); }
+// Conversions between FP32 and FP64 assembled from bits on the integer pipe
+// (on this GPU a conversion instruction costs as much as an FP64 add).
+// Both give the IEEE result: float -> double is exact, double -> float
+// rounds to nearest even.  Values outside the normal float range (zero
+// aside) take the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if ((u << 1) == 0) return __longlong_as_double((long long)sign);   // +-0
+    if (e == 0 || e == 255) return (double)f;
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + (1023 - 127)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+__device__ __forceinline__ float f64_to_f32(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    if ((b << 1) == 0) return __uint_as_float(sign);   // +-0
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -126 || e > 127) return __double2float_rn(d);
+    const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
+    const unsigned m23 = (unsigned)(mant >> 29);
+    const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
+    unsigned r = ((unsigned)(e + 127) << 23) | m23;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) r += 1;   // a carry moves into the exponent
+    return __uint_as_float(sign | r);
+}
+
 // +0 + a for a propensity a (>= +0, or -0 from a -0 rate): the canonical
 // sums start from +0, and adding the first term to +0 only clears the sign
 // of a zero, so the first term is taken with its sign bit cleared (integer
@@ -312,20 +343,6 @@ __device__ __forceinline__ double inversion_uniform(uint64_t seed, uint32_t sim,
     return u01(w.x, w.y);
 }
 
-// True only when inversion certainly returns k = 0 for this (lam, u), that
-// is u <= dexp(-lam), decided without evaluating dexp.  For 0 < lam < 1,
-// e^-lam >= 1 - lam, and dexp(-lam) is within 2^-46 of e^-lam there (its
-// Cody-Waite reduction, Taylor truncation and 15 rounded operations each
-// contribute far less), while RN(1 - lam) is within 2^-54 of 1 - lam.  So
-// dexp(-lam) >= RN(1 - lam) - 2^-45 > RN(RN(1 - lam) - 2^-40), and any u at
-// or below that bound gives k = 0 exactly as the full loop would.  The test
-// is a sufficient condition only; otherwise the caller runs the loop.
-__device__ __forceinline__ bool inversion_zero_sure(double lam, double u)
-{
-    const double lo = (1.0 - lam) - 0x1p-40;
-    return lo > 0.0 && nn_ge(lo, u);
-}
-
 // Inversion by sequential search for 0 < lam < 10: the smallest k with
 // u <= F(k), where p_0 = dexp(-lam), p_k = (p_{k-1} lam) / k and F(k) =
 // F(k-1) + p_k, stopping once a term no longer changes F (the rest of the
@@ -349,6 +366,102 @@ __device__ __forceinline__ long long inversion_draw(double lam, double u, const 
         F = Fn;
     }
     return k;
+}
+
+// ln of the Poisson pmf, k ln lam - lam - ln k!, in FP32 without the
+// cancellation of its large terms.  For k >= 10, with Stirling's series for
+// ln k!, it equals -D - ln(2 pi k)/2 - (1/(12k) - 1/(360k^3)), where
+// D = k ln(k/lam) + lam - k >= 0 is the deviance.  Near k = lam, D is summed
+// from v = (k - lam)/(k + lam) as v (k - lam) + 2k (v^3/3 + v^5/5 + ...),
+// since k ln(k/lam) = 2k atanh(v) and k - lam = v (k + lam) (the saddle-point
+// form of Loader, "Fast and accurate computation of binomial probabilities",
+// 2000); every term there is small, so no precision is lost.
+__device__ __forceinline__ float log_pmf_f32(float k, float lam)
+{
+    if (k < 10.0f) {
+        float f = 1.0f;
+        for (int i = 2; i <= (int)k; ++i) f *= (float)i;   // k! <= 9! is exact in FP32
+        return k * logf(lam) - lam - logf(f);
+    }
+    const float d = k - lam;
+    const float v = d / (k + lam);
+    float D;
+    if (fabsf(v) < 0.25f) {
+        const float v2 = v * v;
+        // sum_{n=1..7} v^(2n+1)/(2n+1); the first omitted term is below 2^-32 of the lead
+        float s = 1.0f / 15.0f;
+        s = s * v2 + 1.0f / 13.0f;
+        s = s * v2 + 1.0f / 11.0f;
+        s = s * v2 + 1.0f / 9.0f;
+        s = s * v2 + 1.0f / 7.0f;
+        s = s * v2 + 1.0f / 5.0f;
+        s = s * v2 + 1.0f / 3.0f;
+        D = v * d + 2.0f * k * (v * v2 * s);
+    } else {
+        D = k * logf(k / lam) + lam - k;
+    }
+    const float rk = 1.0f / k;
+    const float corr = rk * (1.0f / 12.0f - (rk * rk) * (1.0f / 360.0f));
+    return -D - 0.5f * logf(6.283185307f * k) - corr;
+}
+
+// ---------------------------------------------------- certified FP32 decisions
+// On this GPU an FP32 operation is ~64x cheaper than an FP64 one.  Where an
+// FP64 value of the canonical algorithm only feeds a comparison, the
+// comparison is first made on an FP32 evaluation whose distance from the
+// canonical FP64 value is bounded; when the FP32 value lies outside that
+// bound of the decision boundary the decision is the canonical one, and
+// otherwise the caller runs the exact FP64 computation.  Bounds use the
+// documented accuracy of CUDA's expf (2 ulp) and logf (1 ulp) and allow a
+// factor of at least two over the worst case of the rounding of every
+// operation; results are identical to the FP64 path by construction.
+
+// Inversion for 0 < lam < 10: the canonical search stops at the smallest k
+// with u <= F(k).  In FP32, each term p_k = e^-lam lam^k / k! carries a
+// relative error below 8.4e-7 + 2.4e-7 k (expf, the rounding of lam, three
+// roundings per step) and F(k) below 9e-7 + 3e-7 k; u rounds by 2^-25.  The
+// margin 4e-6 + 6e-7 k covers their sum twice.  Returns k, or -1 when a
+// comparison is within the margin (or after 40 terms): then the FP64 search
+// decides.  The FP64 search's early stop (a term below the rounding of F)
+// happens only for u within 1e-15 of 1, which is always within the margin.
+__device__ __forceinline__ int inversion_certain(double lam, double u)
+{
+    const float lf = f64_to_f32(lam);
+    const float uf = f64_to_f32(u);
+    float p = expf(-lf);
+    float F = p;
+    for (int k = 0; k < 40; ++k) {
+        const float m = 4e-6f + 6e-7f * (float)k;
+        if (uf <= F - m) return k;
+        if (!(uf > F + m)) return -1;
+        p = (p * lf) / (float)(k + 1);
+        F = F + p;
+    }
+    return -1;
+}
+
+// PTRS acceptance after the squeeze: accept iff
+//   ln(V inv_alpha / (a / us^2 + b)) <= -lam + k ln lam - ln k!.
+// FP32: the left side from the FP32 images of V, us, a, b (relative error of
+// the argument below 13 * 2^-24, logf within 1 ulp of |ln| <= 40: 5e-6 in
+// all); the right side by log_pmf_f32 (deviance form; the rounding of lam
+// to FP32 moves it by at most |k - lam| 2^-23).  Returns +1 (accept), -1
+// (reject) or 0 (within the margin, or lam >= 2^22: decide in FP64).
+__device__ __forceinline__ int ptrs_accept_certain(double lam, long long k, double V, double us, double a, double b)
+{
+    if (!(lam < 0x1p22)) return 0;
+    const float lf = f64_to_f32(lam), kf = (float)k, af = f64_to_f32(a), bf = f64_to_f32(b);
+    const float usf = f64_to_f32(us), Vf = f64_to_f32(V);
+    const float inv_alpha = 1.1239f + 1.1328f / (bf - 3.4f);
+    const float lhs = logf(Vf * inv_alpha / (af / (usf * usf) + bf));
+    const float rhs = log_pmf_f32(kf, lf);
+    const float d = fabsf(kf - lf);
+    float m = 5e-5f + 4e-6f * (fabsf(rhs) + d);
+    if (k < 10) m += 0x1p-20f * lf;
+    else if (d >= 0.25f * (kf + lf)) m += 4e-6f * kf * fabsf(logf(kf / lf));
+    if (lhs < rhs - m) return 1;
+    if (lhs > rhs + m) return -1;
+    return 0;
 }
 
 // K * 2^-53 for an integer 0 < K < 2^53, exactly, from bits.
@@ -413,6 +526,9 @@ __device__ __forceinline__ long long ptrs_draw(double lam, uint64_t seed, uint32
         if (nn_ge(us, 0.07) && nn_ge(vr, V)) return (k > kCountLimit) ? kCountLimit + 1 : k;
         if (k < 0 || (nn_gt(0.013, us) && nn_gt(V, us))) continue;
         if (k > kCountLimit) return kCountLimit + 1;
+        const int sure = ptrs_accept_certain(lam, k, V, us, a, b);
+        if (sure > 0) return k;
+        if (sure < 0) continue;
         if (!slow_ready) {
             loglam = dlog(lam);
             inv_alpha = 1.1239 + 1.1328 / (b - 3.4);

@@ -12,36 +12,8 @@
 namespace tl {
 namespace fast {
 
-// Conversions between FP32 and FP64 assembled from bits on the integer pipe
-// (on this GPU a conversion instruction costs as much as an FP64 add).
-// Both give the IEEE result: float -> double is exact, double -> float
-// rounds to nearest even.  Values outside the normal float range (zero
-// aside) take the conversion instruction.
-__device__ __forceinline__ double f32_to_f64(float f)
-{
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    if ((u << 1) == 0) return __longlong_as_double((long long)sign);   // +-0
-    if (e == 0 || e == 255) return (double)f;
-    return __longlong_as_double(
-        (long long)(sign | ((unsigned long long)(e + (1023 - 127)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
-}
-
-__device__ __forceinline__ float f64_to_f32(double d)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const unsigned sign = (unsigned)(b >> 63) << 31;
-    if ((b << 1) == 0) return __uint_as_float(sign);   // +-0
-    const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    if (e < -126 || e > 127) return __double2float_rn(d);
-    const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
-    const unsigned m23 = (unsigned)(mant >> 29);
-    const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
-    unsigned r = ((unsigned)(e + 127) << 23) | m23;
-    if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) r += 1;   // a carry moves into the exponent
-    return __uint_as_float(sign | r);
-}
+using f64::f32_to_f64;
+using f64::f64_to_f32;
 
 // Uniform in (0,1) from the top 23 bits of one word: ((w >> 9) + 1/2) 2^-23.
 // It takes the leading bits of the reference mode's 52-bit uniform.
@@ -71,42 +43,7 @@ __device__ __forceinline__ long long inversion(float lam, uint64_t seed, uint32_
     return k;
 }
 
-// ln of the Poisson pmf, k ln lam - lam - ln k!, in FP32 without the
-// cancellation of its large terms.  For k >= 10, with Stirling's series for
-// ln k!, it equals -D - ln(2 pi k)/2 - (1/(12k) - 1/(360k^3)), where
-// D = k ln(k/lam) + lam - k >= 0 is the deviance.  Near k = lam, D is summed
-// from v = (k - lam)/(k + lam) as v (k - lam) + 2k (v^3/3 + v^5/5 + ...),
-// since k ln(k/lam) = 2k atanh(v) and k - lam = v (k + lam) (the saddle-point
-// form of Loader, "Fast and accurate computation of binomial probabilities",
-// 2000); every term there is small, so no precision is lost.
-__device__ __forceinline__ float log_pmf(float k, float lam)
-{
-    if (k < 10.0f) {
-        float f = 1.0f;
-        for (int i = 2; i <= (int)k; ++i) f *= (float)i;   // k! <= 9! is exact in FP32
-        return k * __logf(lam) - lam - __logf(f);
-    }
-    const float d = k - lam;
-    const float v = d / (k + lam);
-    float D;
-    if (fabsf(v) < 0.25f) {
-        const float v2 = v * v;
-        // sum_{n=1..7} v^(2n+1)/(2n+1); the first omitted term is below 2^-32 of the lead
-        float s = 1.0f / 15.0f;
-        s = s * v2 + 1.0f / 13.0f;
-        s = s * v2 + 1.0f / 11.0f;
-        s = s * v2 + 1.0f / 9.0f;
-        s = s * v2 + 1.0f / 7.0f;
-        s = s * v2 + 1.0f / 5.0f;
-        s = s * v2 + 1.0f / 3.0f;
-        D = v * d + 2.0f * k * (v * v2 * s);
-    } else {
-        D = k * logf(k / lam) + lam - k;
-    }
-    const float rk = 1.0f / k;
-    const float corr = rk * (1.0f / 12.0f - (rk * rk) * (1.0f / 360.0f));
-    return -D - 0.5f * logf(6.283185307f * k) - corr;
-}
+using f64::log_pmf_f32;
 
 // PTRS (Hormann 1993) in FP32 for 10 <= lam < kPtrsF32Limit: the candidate
 // integer, the squeeze and the acceptance test (through log_pmf) all in
@@ -128,7 +65,7 @@ __device__ __forceinline__ long long ptrs(float lam, uint64_t seed, uint32_t sim
         if (us >= 0.07f && V <= vr) return (long long)__float2int_rz(kf);   // kf >= 0 here for lam >= 10
         if (kf < 0.0f || (us < 0.013f && V > us)) continue;
         const float lhs = __logf(V * inv_alpha / (a / (us * us) + b));
-        if (lhs <= log_pmf(kf, lam)) return (long long)__float2int_rz(kf);
+        if (lhs <= log_pmf_f32(kf, lam)) return (long long)__float2int_rz(kf);
     }
     return -1;
 }

@@ -23,10 +23,10 @@ struct RefArith {
     __device__ static __forceinline__ double neglog(double u) { return -f64::dlog(u); }
     __device__ static __forceinline__ double tau_of(double E, double a) { return E / a; }
     __device__ static __forceinline__ double mean(double a, double tau) { return a * tau; }
-    __device__ static __forceinline__ bool inv_zero_sure(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
-                                                         uint32_t j)
+    __device__ static __forceinline__ int inv_certain(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                                      uint32_t j)
     {
-        return f64::inversion_zero_sure(lam, f64::inversion_uniform(seed, sim, attempt, j));
+        return f64::inversion_certain(lam, f64::inversion_uniform(seed, sim, attempt, j));
     }
     __device__ static __forceinline__ long long inversion(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
                                                           uint32_t j, const double *inv)

@@ -20,12 +20,12 @@ struct FastArith {
         const int kind = info & 3;
         const int s0 = (info >> 2) & 0x7fff;
         const int s1 = (info >> 17) & 0x7fff;
-        const float cf = fast::f64_to_f32(c);
-        if (kind == 0) return fast::f32_to_f64(cf);
-        if (kind == 1) return fast::f32_to_f64(cf * (float)X[s0 * stride + col]);
-        if (kind == 2) return fast::f32_to_f64((cf * (float)X[s0 * stride + col]) * (float)X[s1 * stride + col]);
+        const float cf = f64::f64_to_f32(c);
+        if (kind == 0) return f64::f32_to_f64(cf);
+        if (kind == 1) return f64::f32_to_f64(cf * (float)X[s0 * stride + col]);
+        if (kind == 2) return f64::f32_to_f64((cf * (float)X[s0 * stride + col]) * (float)X[s1 * stride + col]);
         const int xi = X[s0 * stride + col];
-        return fast::f32_to_f64(cf * (0.5f * ((float)xi * (float)(xi - 1))));
+        return f64::f32_to_f64(cf * (0.5f * ((float)xi * (float)(xi - 1))));
     }
     __device__ static __forceinline__ void uniforms(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t purpose,
                                                     double &ua, double &ub)
@@ -39,29 +39,31 @@ struct FastArith {
     __device__ static __forceinline__ double neglog(double u)
     {
         // u in (0,1) rounded to FP32 stays in (0,1]; -ln 1 = 0 is a zero-length step
-        return fast::f32_to_f64(-logf(fast::f64_to_f32(u)));
+        return f64::f32_to_f64(-logf(f64::f64_to_f32(u)));
     }
     __device__ static __forceinline__ double tau_of(double E, double a)
     {
-        return fast::f32_to_f64(fast::f64_to_f32(E) / fast::f64_to_f32(a));
+        return f64::f32_to_f64(f64::f64_to_f32(E) / f64::f64_to_f32(a));
     }
     __device__ static __forceinline__ double mean(double a, double tau)
     {
-        return fast::f32_to_f64(fast::f64_to_f32(a) * fast::f64_to_f32(tau));
+        return f64::f32_to_f64(f64::f64_to_f32(a) * f64::f64_to_f32(tau));
     }
-    __device__ static __forceinline__ bool inv_zero_sure(double, uint64_t, uint32_t, uint32_t, uint32_t)
+    __device__ static __forceinline__ int inv_certain(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+                                                      uint32_t j)
     {
-        return false;   // the FP32 inversion is cheap enough to run for every positive mean
+        // the FP32 inversion is the fast-mode definition: always decided here
+        return (int)fast::inversion(f64::f64_to_f32(lam), seed, sim, attempt, j);
     }
     __device__ static __forceinline__ long long inversion(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
                                                           uint32_t j, const double *)
     {
-        return fast::inversion(fast::f64_to_f32(lam), seed, sim, attempt, j);
+        return fast::inversion(f64::f64_to_f32(lam), seed, sim, attempt, j);
     }
     __device__ static __forceinline__ long long ptrs(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
                                                      uint32_t j)
     {
-        if (f64::nn_gt((double)fast::kPtrsF32Limit, lam)) return fast::ptrs(fast::f64_to_f32(lam), seed, sim, attempt, j);
+        if (f64::nn_gt((double)fast::kPtrsF32Limit, lam)) return fast::ptrs(f64::f64_to_f32(lam), seed, sim, attempt, j);
         return f64::ptrs_draw(lam, seed, sim, attempt, j);
     }
 };

@@ -37,7 +37,8 @@
 //   neglog(u)                       -ln u
 //   tau_of(E, a)                    E / a (time to the next event)
 //   mean(a, tau)                    the Poisson mean a tau of a leap
-//   inv_zero_sure(lam, stream)      true only if inversion certainly gives 0
+//   inv_certain(lam, stream)        k of the inversion draw when decided
+//                                   cheaply, else -1 (then inversion())
 //   inversion(lam, stream, inv)     k ~ Poisson(lam) for 0 < lam < 10
 //   ptrs(lam, stream)               k ~ Poisson(lam) for lam >= 10
 // Everything else -- the slot tree and its order, the critical set, tau',
@@ -320,7 +321,6 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                     }
                     double Lv[6];
                     const double a0 = slot_tree(s, Lv);
-                    const double ssa_thr = A.ssa_factor / a0;   // the SSA-fallback threshold
 #pragma unroll
                     for (int k = 0; k <= 5; ++k)
                         if (lane < (32 >> k)) V[(node_base(k) + lane) * kStride + L] = Lv[k];
@@ -332,9 +332,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         stL = SSA_STATUS_INVALID;
                         nphase = P_DONE;
                     } else {
-                        // critical set (CGP 2005) and a0c
-                        double sc = 0.0;
-                        bool sc_started = false;   // the first critical term is taken, not added to +0
+                        // critical set (CGP 2005)
                         for (int j = lane; j < M; j += 32) {
                             long long Lj = LLONG_MAX;
                             for (int e = nu_ptr[j]; e < nu_ptr[j + 1]; ++e) {
@@ -347,19 +345,10 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                     Lj = q < Lj ? q : Lj;
                                 }
                             }
-                            const double a = w.a[j];
-                            const bool cr = f64::nn_pos(a) && (Lj < (long long)A.n_c);
-                            w.crit[j] = cr;
-                            if (cr) {
-                                if (sc_started) sc = sc + a;
-                                else sc = a;   // a > 0
-                                sc_started = true;
-                            }
+                            w.crit[j] = f64::nn_pos(w.a[j]) && (Lj < (long long)A.n_c);
                         }
                         for (int i = lane; i < N; i += 32) w.irs[i] = 0;
                         __syncwarp();
-                        double Lc[6];
-                        const double a0c = slot_tree(sc, Lc);
                         for (int j = lane; j < M; j += 32) {
                             if (w.crit[j]) continue;
                             const int info = rinfo[j];
@@ -368,6 +357,19 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             if (kind == 2) w.irs[(info >> 17) & 0x7fff] = 1;
                         }
                         __syncwarp();
+                        {
+                        double sc = 0.0;
+                        bool sc_started = false;   // the first critical term is taken, not added to +0
+                        for (int j = lane; j < M; j += 32) {
+                            if (!w.crit[j]) continue;
+                            const double a = w.a[j];   // > 0
+                            if (sc_started) sc = sc + a;
+                            else sc = a;
+                            sc_started = true;
+                        }
+                        double Lc[6];
+                        const double a0c = slot_tree(sc, Lc);
+                        const double ssa_thr = A.ssa_factor / a0;   // the SSA-fallback threshold
                         // tau' (CGP 2006) over the reactant species of noncritical reactions
                         unsigned long long tmin = 0x7FF0000000000000ull;
                         for (int i = lane; i < N; i += 32) {
@@ -380,8 +382,23 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 const double a = w.a[j];
                                 if (!f64::nn_pos(a)) continue;
                                 const int nv = (signed char)(ent & 0xff);
-                                mu = mu + f64::small_to_double(nv) * a;
-                                sig2 = sig2 + f64::count_to_double(nv * nv) * a;
+                                // nu a and nu^2 a: for |nu| <= 2 exact power-of-two scalings and a
+                                // sign flip (exponent arithmetic on a > 0, normal, far from
+                                // overflow), else the FP64 products; same values either way
+                                const long long ab = f64::dbits(a);
+                                const int ea = (int)(ab >> 52);
+                                const int an = nv < 0 ? -nv : nv;
+                                double tm, ts;
+                                if (an <= 2 && ea >= 1 && ea <= 0x7FC) {
+                                    const long long two = (an == 2) ? (1ll << 52) : 0ll;
+                                    tm = __longlong_as_double((ab + two) | (nv < 0 ? (long long)0x8000000000000000ull : 0ll));
+                                    ts = __longlong_as_double(ab + 2 * two);
+                                } else {
+                                    tm = f64::small_to_double(nv) * a;
+                                    ts = f64::count_to_double(nv * nv) * a;
+                                }
+                                mu = mu + tm;
+                                sig2 = sig2 + ts;
                             }
                             const int xi = X[i * kStride + L];
                             const double xd = f64::count_to_double(xi);
@@ -440,12 +457,13 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 tau = tau1;
                             }
                             // Poisson counts of the noncritical reactions.  A first pass
-                            // forms the means and settles the trivial draws (critical
-                            // reactions, zero means, certain zeros); the rest are queued by
-                            // sampler and drawn in two compacted passes, so a warp runs each
-                            // sampler once per 32 queued draws instead of branching over
-                            // both for every reaction.  Each draw depends only on its own
-                            // mean and stream, so the order is free.
+                            // forms the means and settles what it can (critical reactions,
+                            // zero means, inversion draws decided in FP32 with a certified
+                            // margin); the rest are queued by sampler and drawn in two
+                            // compacted passes, so a warp runs each sampler once per 32
+                            // queued draws instead of branching over both for every
+                            // reaction.  Each draw depends only on its own mean and stream,
+                            // so the order is free.
                             int krej = 0, kover = 0;
                             long long ksum = 0;
                             int n_inv = 0, n_ptrs = 0;
@@ -466,7 +484,9 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                                 kj = f64::kCountLimit + 1;
                                                 kover = 1;
                                             } else if (f64::dbits(lam) < f64::dbits(10.0)) {
-                                                if (!Arith::inv_zero_sure(lam, GL.seed, sL, attL, (uint32_t)j)) cls = 1;
+                                                const int kc = Arith::inv_certain(lam, GL.seed, sL, attL, (uint32_t)j);
+                                                if (kc >= 0) kj = kc;
+                                                else cls = 1;
                                             } else {
                                                 cls = 2;
                                             }
@@ -542,6 +562,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             tL = clamp ? t_stop : tL + tau;
                             lpL += 1;
                             break;
+                        }
                         }
                     }
                 }
