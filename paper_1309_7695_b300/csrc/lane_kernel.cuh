@@ -357,7 +357,63 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             if (kind == 2) w.irs[(info >> 17) & 0x7fff] = 1;
                         }
                         __syncwarp();
+                        // Screen: the canonical decision "tau' < ssa_factor / a0" (SSA
+                        // block) is often certain from FP32.  An FP32 evaluation bounds
+                        // every tau' term from above: mu and sigma^2 summed in FP32 from
+                        // the FP32 images of a_j are within (n + 4) 2^-20 of the sum of
+                        // |nu a| of the FP64 sums, and bound = max(eps x / g, 1) within
+                        // 2^-20 relative; the upper bounds carry a further 1e-4 and the
+                        // threshold's lower bound 1e-4.  A term whose mu is not certainly
+                        // nonzero is left out (a minimum over fewer terms is still an
+                        // upper bound).  When the bound on tau' lies below the bound on
+                        // the threshold, the canonical decision is the SSA block, and the
+                        // FP64 sums, divisions and the a0c tree are skipped.
+                        bool certain_ssa = false;
                         {
+                            unsigned qmin = 0x7F800000u;   // +inf as float bits
+                            for (int i = lane; i < N; i += 32) {
+                                if (!w.irs[i]) continue;
+                                float muf = 0.0f, s2f = 0.0f, absf = 0.0f;
+                                int n = 0;
+                                for (int e = tr_ptr[i]; e < tr_ptr[i + 1]; ++e) {
+                                    const int ent = tr_ent[e];
+                                    const int j = ent >> 8;
+                                    if (w.crit[j]) continue;
+                                    const double a = w.a[j];
+                                    if (!f64::nn_pos(a)) continue;
+                                    const float af = f64::f64_to_f32(a);
+                                    const float nvf = (float)(signed char)(ent & 0xff);
+                                    muf = muf + nvf * af;
+                                    s2f = s2f + (nvf * nvf) * af;
+                                    absf = absf + fabsf(nvf) * af;
+                                    ++n;
+                                }
+                                if (n == 0) continue;
+                                const int xi = X[i * kStride + L];
+                                const float xf = (float)xi;
+                                const int h = hor[i];
+                                float bf = (float)A.eps * xf;
+                                if (h == 2 || (h != 1 && xi < 2)) bf = bf * 0.5f;
+                                else if (h != 1) bf = bf / (2.0f + 1.0f / (xf - 1.0f));
+                                bf = fmaxf(bf, 1.0f) * 1.000001f;   // >= canonical bound
+                                const float err = (float)(n + 4) * 0x1p-20f * absf;
+                                const float amu = fabsf(muf);
+                                if (amu > 2.0f * err) {
+                                    const float q1 = (bf * 1.0001f) / (amu - err);
+                                    qmin = min(qmin, __float_as_uint(q1));
+                                }
+                                const float q2 = ((bf * bf) * 1.0002f) / (s2f * (1.0f - (float)(n + 4) * 0x1p-20f));
+                                if (q2 > 0.0f) qmin = min(qmin, __float_as_uint(q2));
+                            }
+                            qmin = __reduce_min_sync(kFull, qmin);
+                            const float thr_lo = ((float)A.ssa_factor / f64::f64_to_f32(a0)) * 0.9999f;
+                            certain_ssa = __uint_as_float(qmin) < thr_lo;
+                        }
+                        if (certain_ssa) {
+                            nphase = P_SSA;
+                            nleft = A.ssa_block;
+                            nfirst = 1;
+                        } else {
                         double sc = 0.0;
                         bool sc_started = false;   // the first critical term is taken, not added to +0
                         for (int j = lane; j < M; j += 32) {
@@ -440,9 +496,9 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             attL = attL + 1;
                             double u_tau, u_sel;
                             Arith::uniforms(GL.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
-                            const double tau2 = f64::nn_pos(a0c) ? Arith::tau_of(Arith::neglog(u_tau), a0c) : kInf;
                             const double t_stop = (ksL < S) ? tnL : t_end;
                             const double delta = t_stop - tL;
+                            const double tau2 = f64::nn_pos(a0c) ? Arith::tau_of(Arith::neglog(u_tau), a0c) : kInf;
                             double tau;
                             int jc = -1;
                             bool clamp = false;
@@ -563,7 +619,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             lpL += 1;
                             break;
                         }
-                        }
+                        }   // not certain_ssa
                     }
                 }
                 __syncwarp();

@@ -221,3 +221,28 @@ def test_ssa_screen_never_contradicts_the_canonical_decision(oracle_lib):
                 assert q["tau1"] < 10.0 / q["a0"], (net_seed, q["tau1"], 10.0 / q["a0"])
     assert total > 500
     assert certain > 0.2 * total   # the screen settles a good share of SSA decisions
+
+
+def tau2_screen_model(u, a0c, m):
+    """float32 replay of the screen that skips tau'' = -ln(u)/a0c when it is
+    certainly larger than m = min(tau', delta)."""
+    a0cf = f32(a0c)
+    Ef = -np.log(f32(u))
+    lo = f32(max(f32(Ef * f32(0.9999)) - f32(2.0 ** -20), f32(0.0)) / f32(a0cf * f32(1.0001)))
+    return bool(a0cf >= f32(2.0 ** -126) and lo <= f32(2.0 ** 127) and float(lo) > m)
+
+
+def test_tau2_screen_is_a_lower_bound(oracle_lib):
+    rng = np.random.default_rng(24)
+    n = 200_000
+    u = rng.random(n)
+    u[:1000] = 1.0 - rng.random(1000) * 2.0 ** -30        # -ln u tiny
+    a0c = np.exp(rng.uniform(-30, 30, n))
+    tau2 = -oracle_lib.log_array(u) / a0c                 # canonical E / a0c
+    m = tau2 * np.exp(rng.normal(0.0, 1e-3, n))           # thresholds close to tau''
+    skipped = 0
+    for i in range(n):
+        if tau2_screen_model(u[i], a0c[i], m[i]):
+            skipped += 1
+            assert tau2[i] > m[i], (u[i], a0c[i], m[i])
+    assert skipped > 0.3 * n
