@@ -335,6 +335,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fast", action="store_true")
+    ap.add_argument("--no-moments", action="store_true")
     # profiling / sweep knobs; the reported benchmark uses the defaults
     ap.add_argument("--sims", type=int, default=None, help="override the simulations per GPU (profiling)")
     ap.add_argument("--cap", type=int, default=None, help="override the per-simulation attempt cap (profiling)")
@@ -464,6 +465,30 @@ def main():
         fast = {"value": ff / ft, "unit": "firings/s", "sim_steps_per_s": fsteps / ft, "ms_per_step": ft * 1e3 / args.steps,
                 "vs_fp64": (ff / ft) / (fir / t_max), "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'"}
 
+    moments = None
+    if not args.no_moments and args.schedule == "streams":
+        # the same batches with sweep moments accumulated on the device instead of
+        # trajectories written (ssa_simulate_moments_dev), K batches in flight
+        o = options(abi.SSA_FP64_REF)
+        means = [torch.empty((S, N), dtype=torch.float64, device=dev) for _ in range(args.steps)]
+        varis = [torch.empty((S, N), dtype=torch.float64, device=dev) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            side[k].wait_event(e0)
+            abi.ssa_simulate_moments_dev(model, p, x, batch.t_end, T, means[k], varis[k], sts[k], seed=1000 + k,
+                                         opts=o, sim_offset=sim_offset, stream=side[k])
+            stream.wait_stream(side[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mt = e0.elapsed_time(e1) / 1e3
+        mf = sum(float(sts[k].cpu().numpy().view(abi.STATS_DTYPE)["firings"].sum()) for k in range(args.steps))
+        mt, (mf,) = shard.reduce_run(mt, [mf], device=dev)
+        moments = {"value": mf / mt, "unit": "firings/s", "ms_per_step": mt * 1e3 / args.steps,
+                   "vs_trajectories": (mf / mt) / (fir / t_max),
+                   "output_bytes_per_step": int(2 * S * N * 8), "trajectory_bytes_per_step": int(n * S * N * 4)}
+
     e2e = None
     if not args.no_e2e:
         # host-buffer path: pinned inputs -> ssa_submit_batch (H2D inside, one job and stream per
@@ -511,7 +536,7 @@ def main():
                                         else KERNEL_NAMES.get(args.layout, "lane_kernel<RefArith, false>")),
                              "peak_source": "nominal B300 FP64 1.25 TFLOP/s, one operation per multiply-add "
                                             "(of nominal; the measured scalar FP64 issue rate is 0.46 T op/s)"},
-                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "fast_mode": fast}
+                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "fast_mode": fast, "moments_mode": moments}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_rate(batch)
         print(json.dumps(line), flush=True)

@@ -153,6 +153,46 @@ int ssa_simulate_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
                      const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
                      void *stream);
 
+/* Sweep moments instead of trajectories (the sweep post-processing of the
+ * paper's "Aims and motivation": parameter sweeps summarised across
+ * replicates).  Simulates like ssa_simulate_dev (same arguments, same random
+ * streams, lane layout) but writes no samples array: while recording, every
+ * count x of sample k, species i is added to exact integer sums S1 = sum x
+ * and S2 = sum x^2 over the n_sims simulations, and the call ends with
+ *   mean[k][i] = RN(RN(S1) / RN(n_sims)),
+ *   var[k][i]  = RN(RN(n_sims S2 - S1^2) / RN(n_sims (n_sims - 1)))
+ * (unbiased variance, 0 when n_sims < 2), DEVICE arrays [n_samples][N] of
+ * double, caller-owned.  The results are fixed functions of the integer
+ * sums, whatever order the simulations finish in.  This avoids the
+ * n_sims * n_samples * N * 4-byte trajectory array when only moments are
+ * needed.  Allocates (stream-ordered) 24 * n_samples * N bytes of
+ * accumulators and frees them on `stream`.  SSA_EINVAL for n_sims < 1,
+ * n_samples < 1 or null mean/var; SSA_EUNSUPPORTED with the warp layout. */
+int ssa_simulate_moments_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
+                             const double *params, const int32_t *x0, double t_end,
+                             const double *sample_times, int32_t n_samples, uint64_t seed,
+                             const ssa_options *opts, double *mean, double *var, ssa_sim_stats *stats,
+                             void *stream);
+
+/* Deterministic counterpart of a sweep: the reaction-rate equations (the
+ * paper's Methods section: for abundant species the state follows
+ * dX/dt = sum_j nu_j a_j(X) with continuous X; a 2X reaction has the
+ * mean-field propensity c x^2/2), one ODE system per parameter set,
+ * integrated by the Dormand-Prince 5(4) pair with a power-of-two step
+ * controller: h starts at sample_times[n_samples-1] / 64; a step is accepted
+ * when max_i |e_i| / (atol + rtol max(|x_i|, |x_new_i|)) <= 1, after which h
+ * doubles when that error is <= 2^-6 (unless the step was shortened to land
+ * on a sample time); a rejected step halves the step it tried.  DEVICE
+ * arrays: params [n_sims][M], x0 [n_sims][N] int32 (initial amounts),
+ * sample_times [n_samples] non-decreasing and >= 0, out [n_sims][n_samples][N]
+ * double, stats [n_sims] (may be NULL; leaps = accepted steps, rejected =
+ * rejected steps; status STEP_LIMIT after max_steps steps, INVALID for a
+ * non-finite state, after which the samples repeat the last state).
+ * SSA_EINVAL for rtol or atol not finite and > 0 or max_steps < 1. */
+int ssa_integrate_rre_dev(ssa_model_t model, int64_t n_sims, const double *params, const int32_t *x0,
+                          const double *sample_times, int32_t n_samples, double rtol, double atol,
+                          int64_t max_steps, double *out, ssa_sim_stats *stats, void *stream);
+
 /* Same as ssa_simulate_dev, for callers that cannot allocate device memory
  * (for example code that runs inside an allocator's callbacks, or programs
  * that reserve all device memory up front).  It calls no cudaMalloc,

@@ -87,6 +87,10 @@ def lib():
             ctypes.c_int64, vp, ctypes.c_int64, vp, vp, ctypes.c_double, vp, ctypes.c_int32,
             ctypes.c_uint64, ctypes.POINTER(Opts), vp, vp, ctypes.c_int]
         L.oracle_simulate.restype = ctypes.c_int
+        L.oracle_rre.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp,
+            ctypes.c_int64, vp, vp, vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64, vp, vp]
+        L.oracle_rre.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -234,3 +238,46 @@ __all__ = ["simulate", "simulate_batch", "philox", "log_array", "exp_array", "ln
            "STATUS_NAMES", "num_threads"]
 
 _ = os  # keep import for path helpers used by build
+
+
+def sample_moments(samples):
+    """Per (sample time, species) mean and unbiased variance of the counts
+    across simulations, from exact integer sums: with n simulations,
+    S1 = sum x and S2 = sum x^2 (Python integers), mean = S1 / n and
+    var = (n S2 - S1^2) / (n (n - 1)) (0 for n < 2), each converted to double
+    once and divided once (correctly rounded, as the engine's sweep moments
+    are defined).  samples: [n, S, N] int32."""
+    x = np.asarray(samples)
+    n = int(x.shape[0])
+    S1 = x.astype(np.int64).sum(axis=0)
+    S2 = (x.astype(object) ** 2).sum(axis=0)
+    mean = np.empty(S1.shape, dtype=np.float64)
+    var = np.zeros(S1.shape, dtype=np.float64)
+    for idx in np.ndindex(S1.shape):
+        s1 = int(S1[idx])
+        mean[idx] = float(s1) / float(n)
+        if n >= 2:
+            var[idx] = float(n * int(S2[idx]) - s1 * s1) / float(n * (n - 1))
+    return mean, var
+
+
+def rre_simulate(network, params, x0, sample_times, rtol=1e-8, atol=1e-8, max_steps=1_000_000):
+    """Deterministic reaction-rate-equation trajectories of a batch (the
+    canonical Dormand-Prince 5(4) integration of oracle_rre): params [R, M],
+    x0 [R, N] (counts, as initial concentrations), sample_times [S].
+    Returns (states [R, S, N] float64, stats [R])."""
+    csr = network.csr()
+    N, M = network.n_species, network.n_reactions
+    params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, M)
+    x0 = np.ascontiguousarray(x0, dtype=np.int32).reshape(-1, N)
+    T = np.ascontiguousarray(sample_times, dtype=np.float64)
+    R, S = params.shape[0], len(T)
+    out = np.zeros((R, S, N), dtype=np.float64)
+    stats = np.zeros(R, dtype=STATS_DTYPE)
+    rc = lib().oracle_rre(N, M, _ptr(csr["react_ptr"]), _ptr(csr["react_species"]), _ptr(csr["react_coef"]),
+                          _ptr(csr["prod_ptr"]), _ptr(csr["prod_species"]), _ptr(csr["prod_coef"]),
+                          R, _ptr(params), _ptr(x0), _ptr(T), S, float(rtol), float(atol), int(max_steps),
+                          _ptr(out), _ptr(stats))
+    if rc != 0:
+        raise ValueError("invalid model")
+    return out, stats

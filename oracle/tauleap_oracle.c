@@ -806,6 +806,165 @@ int oracle_simulate(int32_t N, int32_t M,
 
 
 /* ------------------------------------------------------------------ */
+/* Reaction-rate equations: deterministic integration of a batch         */
+/* ------------------------------------------------------------------ */
+/* The mean-field model of the network (Methods: for abundant species the
+ * state follows the reaction-rate equations dX/dt = sum_j nu_j a_j(X) with
+ * continuous X; the stochastic 2X propensity c x(x-1)/2 becomes c x^2/2),
+ * one system per parameter set, integrated by the Dormand-Prince 5(4)
+ * pair (Dormand & Prince, J. Comput. Appl. Math. 6, 1980) with its FSAL
+ * property and a power-of-two step controller:
+ *   - h starts at t_last / 64 (t_last = the last sample time);
+ *   - a step whose scaled error err = max_i |e_i| / (atol + rtol max(|x_i|,
+ *     |x_new_i|)) is <= 1 is accepted; after an accepted step that was not
+ *     shortened to land on a sample time, h doubles when err <= 2^-6;
+ *   - a rejected step halves the step it tried;
+ *   - a step that would pass the next sample time is shortened to end on it
+ *     exactly, and the state there is recorded.
+ * Every quantity is one correctly rounded IEEE operation in the order
+ * written.  Accepted steps are counted in stats.leaps, rejected ones in
+ * stats.rejected; accepted + rejected >= max_steps stops the system with
+ * STEP_LIMIT, a non-finite state with INVALID, and the remaining samples
+ * repeat the last state. */
+static const double DP_A21 = 1.0 / 5.0;
+static const double DP_A31 = 3.0 / 40.0, DP_A32 = 9.0 / 40.0;
+static const double DP_A41 = 44.0 / 45.0, DP_A42 = -56.0 / 15.0, DP_A43 = 32.0 / 9.0;
+static const double DP_A51 = 19372.0 / 6561.0, DP_A52 = -25360.0 / 2187.0, DP_A53 = 64448.0 / 6561.0,
+                    DP_A54 = -212.0 / 729.0;
+static const double DP_A61 = 9017.0 / 3168.0, DP_A62 = -355.0 / 33.0, DP_A63 = 46732.0 / 5247.0,
+                    DP_A64 = 49.0 / 176.0, DP_A65 = -5103.0 / 18656.0;
+static const double DP_B1 = 35.0 / 384.0, DP_B3 = 500.0 / 1113.0, DP_B4 = 125.0 / 192.0,
+                    DP_B5 = -2187.0 / 6784.0, DP_B6 = 11.0 / 84.0;
+/* error weights b - b*, b* the embedded fourth-order weights */
+static const double DP_E1 = 35.0 / 384.0 - 5179.0 / 57600.0, DP_E3 = 500.0 / 1113.0 - 7571.0 / 16695.0,
+                    DP_E4 = 125.0 / 192.0 - 393.0 / 640.0, DP_E5 = -2187.0 / 6784.0 - (-92097.0 / 339200.0),
+                    DP_E6 = 11.0 / 84.0 - 187.0 / 2100.0, DP_E7 = 0.0 - 1.0 / 40.0;
+
+/* f = dX/dt at state x: a_j by mass action (mean-field), then per species
+ * the sum over the reactions that change it, in increasing j. */
+static void rre_rhs(const model_t *m, const double *c, const double *x, double *a, double *f)
+{
+    for (int j = 0; j < m->M; ++j) {
+        switch (m->r_kind[j]) {
+        case 0: a[j] = c[j]; break;
+        case 1: a[j] = c[j] * x[m->r_sp0[j]]; break;
+        case 2: a[j] = (c[j] * x[m->r_sp0[j]]) * x[m->r_sp1[j]]; break;
+        default: a[j] = c[j] * ((x[m->r_sp0[j]] * x[m->r_sp0[j]]) * 0.5); break;
+        }
+    }
+    for (int i = 0; i < m->N; ++i) f[i] = 0.0;
+    int *started = calloc((size_t)m->N, sizeof(int));
+    for (int j = 0; j < m->M; ++j) {
+        for (int e = m->nu_ptr[j]; e < m->nu_ptr[j + 1]; ++e) {
+            int i = m->nu_sp[e];
+            double t = (double)m->nu_val[e] * a[j];
+            f[i] = started[i] ? f[i] + t : t;
+            started[i] = 1;
+        }
+    }
+    free(started);
+}
+
+static void rre_one(const model_t *m, const double *c, const int32_t *x0i, const double *T, int S,
+                    double rtol, double atol, int64_t max_steps, double *out, oracle_stats *st)
+{
+    const int N = m->N;
+    size_t NN = (size_t)(N > 0 ? N : 1), MM = (size_t)(m->M > 0 ? m->M : 1);
+    double *x = malloc(sizeof(double) * NN), *xs = malloc(sizeof(double) * NN), *xn = malloc(sizeof(double) * NN);
+    double *k[8], *a = malloc(sizeof(double) * MM);
+    for (int q = 1; q <= 7; ++q) k[q] = malloc(sizeof(double) * NN);
+    for (int i = 0; i < N; ++i) x[i] = (double)x0i[i];
+    memset(st, 0, sizeof *st);
+    st->status = ST_OK;
+    double t = 0.0;
+    double h = (S > 0) ? T[S - 1] / 64.0 : 0.0;
+    rre_rhs(m, c, x, a, k[1]);
+    int ks = 0;
+    while (ks < S) {
+        const double target = T[ks];
+        while (t < target && st->status == ST_OK) {
+            if (st->leaps + st->rejected >= max_steps) { st->status = ST_STEP_LIMIT; break; }
+            double hh = h;
+            int clamped = 0;
+            if (t + hh >= target) { hh = target - t; clamped = 1; }
+            for (int i = 0; i < N; ++i) xs[i] = x[i] + hh * (DP_A21 * k[1][i]);
+            rre_rhs(m, c, xs, a, k[2]);
+            for (int i = 0; i < N; ++i) { double s = DP_A31 * k[1][i]; s = s + DP_A32 * k[2][i]; xs[i] = x[i] + hh * s; }
+            rre_rhs(m, c, xs, a, k[3]);
+            for (int i = 0; i < N; ++i) {
+                double s = DP_A41 * k[1][i]; s = s + DP_A42 * k[2][i]; s = s + DP_A43 * k[3][i];
+                xs[i] = x[i] + hh * s;
+            }
+            rre_rhs(m, c, xs, a, k[4]);
+            for (int i = 0; i < N; ++i) {
+                double s = DP_A51 * k[1][i]; s = s + DP_A52 * k[2][i]; s = s + DP_A53 * k[3][i]; s = s + DP_A54 * k[4][i];
+                xs[i] = x[i] + hh * s;
+            }
+            rre_rhs(m, c, xs, a, k[5]);
+            for (int i = 0; i < N; ++i) {
+                double s = DP_A61 * k[1][i]; s = s + DP_A62 * k[2][i]; s = s + DP_A63 * k[3][i]; s = s + DP_A64 * k[4][i];
+                s = s + DP_A65 * k[5][i];
+                xs[i] = x[i] + hh * s;
+            }
+            rre_rhs(m, c, xs, a, k[6]);
+            for (int i = 0; i < N; ++i) {
+                double s = DP_B1 * k[1][i]; s = s + DP_B3 * k[3][i]; s = s + DP_B4 * k[4][i]; s = s + DP_B5 * k[5][i];
+                s = s + DP_B6 * k[6][i];
+                xn[i] = x[i] + hh * s;
+            }
+            rre_rhs(m, c, xn, a, k[7]);
+            double err = 0.0;
+            int bad = 0;
+            for (int i = 0; i < N; ++i) {
+                double s = DP_E1 * k[1][i]; s = s + DP_E3 * k[3][i]; s = s + DP_E4 * k[4][i]; s = s + DP_E5 * k[5][i];
+                s = s + DP_E6 * k[6][i]; s = s + DP_E7 * k[7][i];
+                double ei = fabs(hh * s);
+                double sc = atol + rtol * fmax(fabs(x[i]), fabs(xn[i]));
+                double r = ei / sc;
+                if (!(r == r) || !isfinite(xn[i])) bad = 1;
+                if (r > err) err = r;
+            }
+            if (bad) { st->status = ST_INVALID; break; }
+            if (err <= 1.0) {
+                t = clamped ? target : t + hh;
+                for (int i = 0; i < N; ++i) { x[i] = xn[i]; k[1][i] = k[7][i]; }
+                st->leaps += 1;
+                if (!clamped && err <= 0x1p-6) h = 2.0 * h;
+            } else {
+                st->rejected += 1;
+                h = hh * 0.5;
+            }
+        }
+        for (int i = 0; i < N; ++i) out[(size_t)ks * N + i] = x[i];
+        ++ks;
+    }
+    st->attempts = st->leaps + st->rejected;
+    st->t_final = t;
+    free(x); free(xs); free(xn); free(a);
+    for (int q = 1; q <= 7; ++q) free(k[q]);
+}
+
+int oracle_rre(int32_t N, int32_t M,
+               const int32_t *react_ptr, const int32_t *react_species, const int32_t *react_coef,
+               const int32_t *prod_ptr, const int32_t *prod_species, const int32_t *prod_coef,
+               int64_t n_rows, const double *params, const int32_t *x0, const double *sample_times, int32_t S,
+               double rtol, double atol, int64_t max_steps, double *out, oracle_stats *stats)
+{
+    model_t m;
+    if (model_build(&m, N, M, react_ptr, react_species, react_coef, prod_ptr, prod_species, prod_coef) != 0) {
+        model_free(&m);
+        return -1;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < n_rows; ++r)
+        rre_one(&m, params + (size_t)r * M, x0 + (size_t)r * N, sample_times, S, rtol, atol, max_steps,
+                out + (size_t)r * S * N, stats + r);
+    model_free(&m);
+    return 0;
+}
+
+
+/* ------------------------------------------------------------------ */
 /* Bulk entry points used by the pinning tests                           */
 /* ------------------------------------------------------------------ */
 void oracle_log_array(const double *x, double *y, int64_t n)

@@ -43,7 +43,7 @@ SSA_LAYOUT_LANE = 2
 
 EXPORTED = [
     "ssa_default_options", "ssa_load_model", "ssa_free_model", "ssa_model_info",
-    "ssa_simulate_dev", "ssa_simulate_dev_noalloc", "ssa_simulate_multi_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
+    "ssa_simulate_dev", "ssa_simulate_moments_dev", "ssa_integrate_rre_dev", "ssa_simulate_dev_noalloc", "ssa_simulate_multi_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
     "ssa_release_job", "ssa_last_error", "ssa_abi_version",
     "ssa_server_default_config", "ssa_server_create", "ssa_server_submit", "ssa_server_poll", "ssa_server_wait",
     "ssa_server_fetch", "ssa_server_stats", "ssa_server_destroy", "ssa_server_last_error",
@@ -118,6 +118,9 @@ def lib():
     L.ssa_model_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.ssa_simulate_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp, vp, vp]
     L.ssa_simulate_dev_noalloc.argtypes = L.ssa_simulate_dev.argtypes
+    L.ssa_integrate_rre_dev.argtypes = [vp, i64, vp, vp, vp, i32, f64, f64, i64, vp, vp, vp]
+    L.ssa_simulate_moments_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp, vp,
+                                           vp, vp]
     L.ssa_simulate_multi_dev.argtypes = [i32, ctypes.POINTER(Group), ctypes.POINTER(Options), vp]
     L.ssa_submit_batch.argtypes = [vp, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp,
                                    ctypes.POINTER(vp)]
@@ -216,6 +219,36 @@ def ssa_simulate_dev(model: Model, params, x0, t_end, sample_times, samples, sta
     _check(lib().ssa_simulate_dev(model.handle, n, int(sim_offset), _ptr(params), _ptr(x0), float(t_end),
                                   _ptr(sample_times), int(sample_times.numel()), int(seed), ctypes.byref(o),
                                   _ptr(samples), _ptr(stats), ctypes.c_void_p(int(handle))))
+
+
+def ssa_simulate_moments_dev(model: Model, params, x0, t_end, sample_times, mean, var, stats=None, seed=0,
+                             opts=None, sim_offset=0, stream=None):
+    """Simulate like ssa_simulate_dev but write only the sweep moments:
+    mean, var [S, N] float64 torch CUDA tensors (outputs)."""
+    n = int(params.shape[0]) if params.dim() == 2 else 0
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    o = opts if opts is not None else ssa_default_options()
+    _check(lib().ssa_simulate_moments_dev(model.handle, n, int(sim_offset), _ptr(params), _ptr(x0), float(t_end),
+                                          _ptr(sample_times), int(sample_times.numel()), int(seed), ctypes.byref(o),
+                                          _ptr(mean), _ptr(var), _ptr(stats), ctypes.c_void_p(int(handle))))
+
+
+def ssa_integrate_rre_dev(model: Model, params, x0, sample_times, out, stats=None, rtol=1e-8, atol=1e-8,
+                          max_steps=1_000_000, stream=None):
+    """Reaction-rate-equation trajectories of a batch on device tensors:
+    params [n, M] float64, x0 [n, N] int32, sample_times [S] float64,
+    out [n, S, N] float64 (output), stats [n * 56] uint8 or None."""
+    n = int(params.shape[0]) if params.dim() == 2 else 0
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().ssa_integrate_rre_dev(model.handle, n, _ptr(params), _ptr(x0), _ptr(sample_times),
+                                       int(sample_times.numel()), float(rtol), float(atol), int(max_steps),
+                                       _ptr(out), _ptr(stats), ctypes.c_void_p(int(handle))))
 
 
 def ssa_simulate_dev_noalloc(model: Model, params, x0, t_end, sample_times, samples, stats=None, seed=0,

@@ -28,6 +28,8 @@ UNITS = {
     "kernel_lane_f64.cu": ["-fmad=false"],
     "kernel_lane_fast.cu": [],
     "server.cu": [],
+    "moments.cu": [],
+    "kernel_rre.cu": ["-fmad=false"],
 }
 
 

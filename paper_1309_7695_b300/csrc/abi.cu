@@ -272,7 +272,7 @@ namespace {
 int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
                       const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
                       uint64_t seed, const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
-                      void *stream, unsigned long long *counter_in)
+                      void *stream, unsigned long long *counter_in, unsigned long long *moments = nullptr)
 {
     if (!m) return fail(SSA_EINVAL, "null model");
     ssa_options o;
@@ -284,7 +284,8 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     if (n_samples < 0) return fail(SSA_EINVAL, "n_samples < 0");
     if (!(t_end >= 0.0) || !std::isfinite(t_end)) return fail(SSA_EINVAL, "t_end must be finite and >= 0");
     if (n_sims == 0) return SSA_OK;
-    if (!params || !x0 || (n_samples > 0 && (!sample_times || !samples))) return fail(SSA_EINVAL, "null device array");
+    if (!params || !x0 || (n_samples > 0 && (!sample_times || (!samples && !moments))))
+        return fail(SSA_EINVAL, "null device array");
     DeviceGuard g(m->device);
     if (!g.ok) return fail(SSA_ECUDA, "cannot select the model's device");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -296,6 +297,8 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     int layout = o.layout;
     if (layout == SSA_LAYOUT_AUTO)
         layout = (tl::lane_f64_smem_bytes(m->L, 1) <= (size_t)smem_optin) ? SSA_LAYOUT_LANE : SSA_LAYOUT_WARP;
+    if (moments && layout != SSA_LAYOUT_LANE)
+        return fail(SSA_EUNSUPPORTED, "sweep moments are accumulated by the lane layout only");
     auto smem_of = [&](int w) {
         return layout == SSA_LAYOUT_LANE ? tl::lane_f64_smem_bytes(m->L, w) : tl::warp_f64_smem_bytes(m->L, w);
     };
@@ -334,6 +337,7 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     a.sims_per_warp = spw;
     a.samples = samples;
     a.stats = stats;
+    a.moments = moments;
     void *counter = counter_in;
     if (!counter_in) TL_CUDA(cudaMallocAsync(&counter, sizeof(unsigned long long), s));
     a.work_counter = static_cast<unsigned long long *>(counter);
@@ -399,6 +403,71 @@ int ssa_simulate_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const do
     g_error.clear();
     return simulate_dev_impl(m, n_sims, sim_offset, params, x0, t_end, sample_times, n_samples, seed, opts,
                              samples, stats, stream, nullptr);
+}
+
+int ssa_integrate_rre_dev(ssa_model_t m, int64_t n_sims, const double *params, const int32_t *x0,
+                          const double *sample_times, int32_t n_samples, double rtol, double atol, int64_t max_steps,
+                          double *out, ssa_sim_stats *stats, void *stream)
+{
+    g_error.clear();
+    if (!m) return fail(SSA_EINVAL, "null model");
+    if (n_sims < 0 || n_samples < 0) return fail(SSA_EINVAL, "n_sims and n_samples must be >= 0");
+    if (!(rtol > 0.0) || !(atol > 0.0) || !std::isfinite(rtol) || !std::isfinite(atol))
+        return fail(SSA_EINVAL, "rtol and atol must be finite and > 0");
+    if (max_steps < 1) return fail(SSA_EINVAL, "max_steps must be >= 1");
+    if (n_sims == 0 || n_samples == 0) return SSA_OK;
+    if (!params || !x0 || !sample_times || !out) return fail(SSA_EINVAL, "null device array");
+    DeviceGuard g(m->device);
+    if (!g.ok) return fail(SSA_ECUDA, "cannot select the model's device");
+    int optin = 0;
+    TL_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    if (tl::rre_smem_bytes(m->L) > (size_t)optin) return fail(SSA_EUNSUPPORTED, "network too large for the RRE workspace");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void *counter = nullptr;
+    TL_CUDA(cudaMallocAsync(&counter, sizeof(unsigned long long), s));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = tl::launch_rre(m->L, m->d_blob, n_sims, params, x0, sample_times, n_samples, rtol, atol, max_steps, out,
+                           stats, static_cast<unsigned long long *>(counter), s);
+    cudaError_t e2 = cudaFreeAsync(counter, s);
+    if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("rre: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(SSA_ECUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(e2));
+    return SSA_OK;
+}
+
+int ssa_simulate_moments_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
+                             const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
+                             uint64_t seed, const ssa_options *opts, double *mean, double *var,
+                             ssa_sim_stats *stats, void *stream)
+{
+    g_error.clear();
+    if (!m) return fail(SSA_EINVAL, "null model");
+    if (n_samples <= 0) return fail(SSA_EINVAL, "sweep moments need at least one sample time");
+    if (n_sims <= 0) return fail(SSA_EINVAL, "sweep moments need at least one simulation");
+    if (!mean || !var) return fail(SSA_EINVAL, "null mean/var array");
+    const long long cells = (long long)n_samples * m->L.N;
+    if (cells > (1ll << 30)) return fail(SSA_EINVAL, "too many (sample, species) cells");
+    DeviceGuard g(m->device);
+    if (!g.ok) return fail(SSA_ECUDA, "cannot select the model's device");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void *acc = nullptr;
+    const size_t acc_bytes = sizeof(unsigned long long) * 3 * (size_t)cells;
+    TL_CUDA(cudaMallocAsync(&acc, acc_bytes, s));
+    cudaError_t e = cudaMemsetAsync(acc, 0, acc_bytes, s);
+    int rc = SSA_OK;
+    if (e == cudaSuccess) {
+        rc = simulate_dev_impl(m, n_sims, sim_offset, params, x0, t_end, sample_times, n_samples, seed, opts, nullptr,
+                               stats, stream, nullptr, static_cast<unsigned long long *>(acc));
+        if (rc == SSA_OK)
+            e = tl::launch_moments_finalize(static_cast<const unsigned long long *>(acc), n_sims, (int)cells, mean,
+                                            var, s);
+    }
+    const std::string msg = g_error;
+    cudaError_t e2 = cudaFreeAsync(acc, s);
+    if (rc != SSA_OK) return fail(rc, msg);
+    if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("moments: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(SSA_ECUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(e2));
+    return SSA_OK;
 }
 
 

@@ -76,6 +76,10 @@ struct SimArgs {
     int32_t *samples;
     ssa_sim_stats *stats;
     unsigned long long *work_counter;
+    // sweep moments (single-network lane launches): when non-null, every
+    // recorded count x of cell (k, i) adds x, (x^2 mod 2^32) and (x^2 >> 32)
+    // to moments[(k*N + i)*3 + 0..2]; samples may then be null
+    unsigned long long *moments;
 };
 
 // Shared-memory bytes of one warp's simulation workspace.
@@ -113,6 +117,19 @@ cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, s
 int lane_multi_ref_occupancy(int block_warps, size_t smem);
 cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
 int lane_multi_fast_occupancy(int block_warps, size_t smem);
+
+// Sweep moments (moments.cu): mean[c] and unbiased var[c] of every cell c =
+// k*N + i from the exact integer sums accumulated by the lane kernels.
+cudaError_t launch_moments_finalize(const unsigned long long *acc, long long n, int cells, double *mean, double *var,
+                                    cudaStream_t s);
+
+// Reaction-rate equations, one warp per system (kernel_rre.cu): states
+// out[n][S][N] (double) at the sample times; stats as for simulations (leaps
+// = accepted steps, rejected = rejected steps).
+cudaError_t launch_rre(const ModelLayout &L, const int32_t *blob, int64_t n_sims, const double *params,
+                       const int32_t *x0, const double *T, int32_t S, double rtol, double atol, int64_t max_steps,
+                       double *out, ssa_sim_stats *stats, unsigned long long *counter, cudaStream_t s);
+size_t rre_smem_bytes(const ModelLayout &L);
 
 // Warp-per-simulation FP64 reference kernel (kernel_warp_f64.cu).
 size_t warp_f64_smem_bytes(const ModelLayout &L, int block_warps);

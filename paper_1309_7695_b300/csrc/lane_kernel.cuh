@@ -112,9 +112,25 @@ struct GroupView {
     const double *T;
     int32_t *samples;
     ssa_sim_stats *stats;
+    unsigned long long *moments;
     long long sim_offset, n_sims, first;
     uint64_t seed;
 };
+
+// One recorded count of simulation `row`, sample k, species i: stored in the
+// trajectory array and/or added to the sweep moments of cell (k, i) (exact
+// integer sums: x, and x^2 split at bit 32 so neither word can overflow).
+__device__ __forceinline__ void record_count(const GroupView &G, long long row, int k, int i, int x)
+{
+    if (G.samples) G.samples[((size_t)row * G.S + k) * (size_t)G.N + i] = x;
+    if (G.moments) {
+        unsigned long long *c = G.moments + ((size_t)k * G.N + i) * 3;
+        const unsigned long long ux = (unsigned)x, sq = ux * ux;
+        atomicAdd(c, ux);
+        atomicAdd(c + 1, sq & 0xFFFFFFFFull);
+        atomicAdd(c + 2, sq >> 32);
+    }
+}
 
 __device__ __forceinline__ void view_model(GroupView &G, const int *blob, const ModelLayout &L)
 {
@@ -142,6 +158,7 @@ __device__ __forceinline__ GroupView view_single(const SimArgs &A, const int *sm
     G.T = A.T;
     G.samples = A.samples;
     G.stats = A.stats;
+    G.moments = A.moments;
     G.sim_offset = A.sim_offset;
     G.n_sims = A.n_sims;
     G.first = 0;
@@ -162,6 +179,7 @@ __device__ __forceinline__ GroupView view_group(const GroupArgs *groups, int g)
     G.T = R.T;
     G.samples = R.samples;
     G.stats = R.stats;
+    G.moments = nullptr;
     G.sim_offset = R.sim_offset;
     G.n_sims = R.n_sims;
     G.first = R.first;
@@ -214,8 +232,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
         return Arith::prop(G.rinfo[j], __ldg(G.params + (size_t)row * G.M + j), X, kStride, lane);
     };
     auto lane_record = [&](const GroupView &G, int k) {
-        int *dst = G.samples + ((size_t)row * G.S + k) * (size_t)G.N;
-        for (int i = 0; i < G.N; ++i) dst[i] = X[i * kStride + lane];
+        for (int i = 0; i < G.N; ++i) record_count(G, row, k, i, X[i * kStride + lane]);
     };
     auto lane_build_tree = [&](const GroupView &G) {
         for (int l = 0; l < 32; ++l) {
@@ -293,12 +310,11 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                 long long fiL = fi0;
                 int stL = SSA_STATUS_OK;
                 int nphase = P_TOP, nleft = 0, nfirst = 0;
-                int *rowout = GL.samples + (size_t)rL * S * (size_t)N;
                 const double *cL = GL.params + (size_t)rL * M;
 
                 double tnL = __shfl_sync(kFull, tnext, L);
                 while (ksL < S && tnL <= tL) {
-                    for (int i = lane; i < N; i += 32) rowout[(size_t)ksL * N + i] = X[i * kStride + L];
+                    for (int i = lane; i < N; i += 32) record_count(GL, rL, ksL, i, X[i * kStride + L]);
                     ++ksL;
                     tnL = (ksL < S) ? T[ksL] : kInf;
                 }
@@ -498,7 +514,21 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             Arith::uniforms(GL.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
                             const double t_stop = (ksL < S) ? tnL : t_end;
                             const double delta = t_stop - tL;
-                            const double tau2 = f64::nn_pos(a0c) ? Arith::tau_of(Arith::neglog(u_tau), a0c) : kInf;
+                            // tau'' = -ln(u)/a0c matters only if it can be the smallest of
+                            // tau'' , tau' and delta.  An FP32 lower bound (logf within 1 ulp,
+                            // u and a0c rounded to FP32, 1e-4 slack, 2^-20 absolute for u near
+                            // 1) above min(tau', delta) settles "no critical firing", and +inf
+                            // then stands in for tau'' in the comparisons below.
+                            double tau2 = kInf;
+                            if (f64::nn_pos(a0c)) {
+                                const float a0cf = f64::f64_to_f32(a0c);
+                                const float Ef = -logf(f64::f64_to_f32(u_tau));
+                                const float lo = fmaxf(Ef * 0.9999f - 0x1p-20f, 0.0f) / (a0cf * 1.0001f);
+                                const double m = f64::nn_ge(delta, tau1) ? tau1 : delta;
+                                const bool surely_later = a0cf >= 0x1p-126f && lo <= 0x1p127f &&
+                                                          f64::nn_gt(f64::f32_to_f64(lo), m);
+                                if (!surely_later) tau2 = Arith::tau_of(Arith::neglog(u_tau), a0c);
+                            }
                             double tau;
                             int jc = -1;
                             bool clamp = false;

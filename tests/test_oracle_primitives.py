@@ -174,3 +174,24 @@ def test_canon_select_single_positive(oracle_lib, u):
     v = np.zeros(70)
     v[45] = 2.5
     assert oracle_lib.canon_select(v, u) == 45
+
+
+# ------------------------------------------------------- sweep moments
+
+def test_sample_moments_match_numpy_and_exact_cases(oracle_lib):
+    rng = np.random.default_rng(31)
+    x = rng.integers(0, 2**31 - 1, size=(257, 3, 4)).astype(np.int32)
+    mean, var = oracle_lib.sample_moments(x)
+    xd = x.astype(np.float64)
+    assert np.allclose(mean, xd.mean(axis=0), rtol=1e-15, atol=0)
+    assert np.allclose(var, xd.var(axis=0, ddof=1), rtol=1e-12, atol=0)
+    # closed forms: constant columns have variance 0; 0..n-1 has variance n(n+1)/12
+    c = np.full((10, 1, 1), 7, dtype=np.int32)
+    m, v = oracle_lib.sample_moments(c)
+    assert m[0, 0] == 7.0 and v[0, 0] == 0.0
+    r = np.arange(100, dtype=np.int32).reshape(100, 1, 1)
+    m, v = oracle_lib.sample_moments(r)
+    assert m[0, 0] == 49.5 and v[0, 0] == 100 * 101 / 12
+    one = np.array([[[5]]], dtype=np.int32)
+    m, v = oracle_lib.sample_moments(one)
+    assert m[0, 0] == 5.0 and v[0, 0] == 0.0
