@@ -1,10 +1,13 @@
 // Device arithmetic of the FP64 reference mode.
 //
-// Every function here is a fixed sequence of correctly rounded IEEE-754
-// double operations (add, sub, mul, div, sqrt) plus exact bit manipulation,
-// compiled with -fmad=false so no multiply-add is fused.  A CPU program that
-// performs the same operations in the same order gets bit-identical values.
-// No CUDA math-library transcendental is used.
+// Every function that produces a value of the algorithm is a fixed sequence
+// of correctly rounded IEEE-754 double operations (add, sub, mul, div, sqrt,
+// explicit fma) plus exact bit manipulation, compiled with -fmad=false so no
+// multiply-add is fused.  A CPU program that performs the same operations in
+// the same order gets bit-identical values.  No CUDA math-library function
+// determines a result: CUDA's FP32 expf / logf appear only inside the
+// certified decisions below, which return the canonical decision or defer to
+// the FP64 computation.
 #pragma once
 
 #include <stdint.h>

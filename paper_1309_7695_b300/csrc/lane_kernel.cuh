@@ -42,7 +42,11 @@
 //   inversion(lam, stream, inv)     k ~ Poisson(lam) for 0 < lam < 10
 //   ptrs(lam, stream)               k ~ Poisson(lam) for lam >= 10
 // Everything else -- the slot tree and its order, the critical set, tau',
-// the control flow and counters -- is shared and runs in FP64.
+// the control flow and counters -- is shared and runs in FP64, except that
+// decisions whose FP64 operands only feed a comparison (the SSA-fallback
+// test, whether tau'' can be the step) are first taken in FP32 with a
+// margin that certifies the canonical outcome.  Recorded states go to the
+// trajectory array and/or the sweep-moment sums (record_count).
 #pragma once
 
 #include <climits>
