@@ -15,7 +15,9 @@
  *     Cao, Gillespie & Petzold (J. Chem. Phys. 123, 054104, 2005),
  *   - falling back to blocks of exact SSA steps (direct method) when the
  *     admissible leap is shorter than a few mean reaction times,
- *   - or exact SSA only (SSA_MODE_EXACT).
+ *   - or exact SSA only (SSA_MODE_EXACT),
+ *   - or tau-leaping with Langevin (normal) increments for large leap means
+ *     (SSA_MODE_CLE).
  * Random numbers come from Philox4x32-10 counter-based streams.  A
  * simulation's stream is keyed by (seed, global simulation index), so results
  * do not depend on batch composition, launch shape or sharding.
@@ -67,6 +69,9 @@ extern "C" {
 /* ssa_options.mode */
 #define SSA_MODE_TAU_LEAP 0 /* CGP tau-leaping with critical reactions + SSA fallback */
 #define SSA_MODE_EXACT 1    /* Gillespie direct method only */
+#define SSA_MODE_CLE 2      /* as TAU_LEAP, but a noncritical reaction whose leap mean is >= 1000 fires
+                               max(0, round(mean + sqrt(mean) z)) times, z ~ N(0,1) (chemical Langevin
+                               increment, Marsaglia's polar method on the same stream); lane layout only */
 
 /* ssa_options.precision */
 #define SSA_FP64_REF 0 /* bit-identical to the FP64 reference algorithm */

@@ -22,6 +22,7 @@ from . import build as _build
 
 MODE_TAU_LEAP = 0
 MODE_EXACT_SSA = 1
+MODE_CLE = 2   # tau-leaping with Langevin increments for leap means >= 1000
 STATUS_NAMES = {0: "OK", 1: "STEP_LIMIT", 2: "OVERFLOW", 3: "REJECT_LIMIT", 4: "INVALID"}
 
 
@@ -91,6 +92,8 @@ def lib():
             ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp,
             ctypes.c_int64, vp, vp, vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64, vp, vp]
         L.oracle_rre.restype = ctypes.c_int
+        L.oracle_normal_leap_array.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, vp]
+        L.oracle_normal_leap_array.restype = None
         _lib = L
     return _lib
 
@@ -234,7 +237,7 @@ def num_threads() -> int:
 
 __all__ = ["simulate", "simulate_batch", "philox", "log_array", "exp_array", "lnfact_array",
            "poisson_array", "canon_sum", "canon_select", "leap_quantities", "u01", "log", "exp", "lnfact", "poisson",
-           "default_opts", "Opts", "STATS_DTYPE", "MODE_TAU_LEAP", "MODE_EXACT_SSA",
+           "default_opts", "Opts", "STATS_DTYPE", "MODE_TAU_LEAP", "MODE_EXACT_SSA", "MODE_CLE",
            "STATUS_NAMES", "num_threads"]
 
 _ = os  # keep import for path helpers used by build
@@ -281,3 +284,11 @@ def rre_simulate(network, params, x0, sample_times, rtol=1e-8, atol=1e-8, max_st
     if rc != 0:
         raise ValueError("invalid model")
     return out, stats
+
+
+def normal_leap_array(lam, n, seed=0):
+    """n Langevin increments of mean lam (streams sim = 0..n-1, attempt 1,
+    reaction 0), as the CLE mode draws them for leap means >= 1000."""
+    out = np.empty(n, dtype=np.int64)
+    lib().oracle_normal_leap_array(float(lam), int(seed), int(n), _ptr(out))
+    return out

@@ -51,11 +51,11 @@
 /* status codes and options                                            */
 /* ------------------------------------------------------------------ */
 enum { ST_OK = 0, ST_STEP_LIMIT = 1, ST_OVERFLOW = 2, ST_REJECT_LIMIT = 3, ST_INVALID = 4 };
-enum { MODE_TAU_LEAP = 0, MODE_EXACT_SSA = 1 };
+enum { MODE_TAU_LEAP = 0, MODE_EXACT_SSA = 1, MODE_CLE = 2 };
 enum { PURPOSE_LEAP = 1, PURPOSE_POISSON = 2, PURPOSE_SSA = 3 };
 
 typedef struct {
-    int32_t mode;          /* MODE_TAU_LEAP or MODE_EXACT_SSA */
+    int32_t mode;          /* MODE_TAU_LEAP, MODE_EXACT_SSA or MODE_CLE */
     int32_t n_c;           /* critical threshold on L_j (CGP 2005), 10 */
     double eps;            /* error-control parameter epsilon (CGP 2006), 0.03 */
     double ssa_factor;     /* leap abandoned when tau' < ssa_factor / a0 (CGP 2006), 10 */
@@ -366,6 +366,35 @@ int64_t oracle_poisson(double lam, uint64_t seed, uint32_t sim, uint32_t attempt
         double lhs = oracle_log(V * inv_alpha / (a / (us * us) + b));
         double rhs = -lam + kd * loglam - oracle_lnfact((int64_t)kd);
         if (lhs <= rhs) return (int64_t)kd;
+    }
+    return -1;
+}
+
+/* Langevin increment for a large leap mean (chemical Langevin equation,
+ * Gillespie 2000, cited by the paper as the CLE): the Poisson count of a
+ * reaction whose mean lam is at least CLE_MIN_MEAN is replaced by its normal
+ * approximation rounded to the nearest count, k = max(0, floor(lam +
+ * sqrt(lam) z + 1/2)), z ~ N(0,1) by Marsaglia's polar method (one stream
+ * block per try: v1 = 2u1 - 1, v2 = 2u2 - 1, accepted when 0 < s = v1^2 +
+ * v2^2 < 1, z = v1 sqrt(-2 ln s / s)).  Returns -1 after PTRS_MAX_ITERS
+ * rejected tries and COUNT_LIMIT + 1 for a mean at or above 2^40 or a draw
+ * above the count limit. */
+#define CLE_MIN_MEAN 1000.0
+int64_t oracle_normal_leap(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+{
+    uint32_t w[4];
+    if (!(lam < 0x1p40)) return COUNT_LIMIT + 1;   /* mean beyond the count limit, as for Poisson */
+    for (uint32_t it = 0; it < PTRS_MAX_ITERS; ++it) {
+        draw_block(seed, sim, attempt, PURPOSE_POISSON, j, it, w);
+        double v1 = 2.0 * oracle_u01(w[0], w[1]) - 1.0;
+        double v2 = 2.0 * oracle_u01(w[2], w[3]) - 1.0;
+        double s = v1 * v1 + v2 * v2;
+        if (!(s < 1.0) || !(s > 0.0)) continue;
+        double z = v1 * sqrt((-2.0 * oracle_log(s)) / s);
+        double k = floor((lam + sqrt(lam) * z) + 0.5);
+        if (k < 0.0) return 0;
+        if (k > (double)COUNT_LIMIT) return COUNT_LIMIT + 1;
+        return (int64_t)k;
     }
     return -1;
 }
@@ -709,7 +738,10 @@ static void simulate_one(const model_t *m, const oracle_opts *o, uint64_t seed, 
             int kover = 0, krej = 0;
             for (int j = 0; j < M; ++j) {
                 if (w->crit[j]) { w->k[j] = (j == jc) ? 1 : 0; continue; }
-                int64_t kj = oracle_poisson(w->a[j] * tau, seed, sim, attempt, (uint32_t)j);
+                double lam = w->a[j] * tau;
+                int64_t kj = (o->mode == MODE_CLE && lam >= CLE_MIN_MEAN)
+                                 ? oracle_normal_leap(lam, seed, sim, attempt, (uint32_t)j)
+                                 : oracle_poisson(lam, seed, sim, attempt, (uint32_t)j);
                 if (kj < 0) krej = 1;
                 else if (kj > COUNT_LIMIT) kover = 1;
                 w->k[j] = kj;
@@ -987,6 +1019,12 @@ void oracle_poisson_array(double lam, uint64_t seed, int64_t n, int64_t *out)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) out[i] = oracle_poisson(lam, seed, (uint32_t)i, 1u, 0u);
+}
+
+void oracle_normal_leap_array(double lam, uint64_t seed, int64_t n, int64_t *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_normal_leap(lam, seed, (uint32_t)i, 1u, 0u);
 }
 
 double oracle_canon_sum(const double *v, int32_t M)

@@ -35,6 +35,7 @@ SSA_JOB_FAILED = 3
 
 SSA_MODE_TAU_LEAP = 0
 SSA_MODE_EXACT = 1
+SSA_MODE_CLE = 2
 SSA_FP64_REF = 0
 SSA_FAST = 1
 SSA_LAYOUT_AUTO = 0

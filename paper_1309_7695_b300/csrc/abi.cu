@@ -245,7 +245,10 @@ int ssa_model_info(ssa_model_t m, int32_t *n_species, int32_t *n_reactions)
 
 static int check_options(const ssa_options *o)
 {
-    if (o->mode != SSA_MODE_TAU_LEAP && o->mode != SSA_MODE_EXACT) return fail(SSA_EINVAL, "unknown mode");
+    if (o->mode != SSA_MODE_TAU_LEAP && o->mode != SSA_MODE_EXACT && o->mode != SSA_MODE_CLE)
+        return fail(SSA_EINVAL, "unknown mode");
+    if (o->mode == SSA_MODE_CLE && o->layout == SSA_LAYOUT_WARP)
+        return fail(SSA_EUNSUPPORTED, "Langevin increments run in the lane layout only");
     if (o->precision != SSA_FP64_REF && o->precision != SSA_FAST) return fail(SSA_EINVAL, "unknown precision");
     if (o->precision == SSA_FAST && o->layout == SSA_LAYOUT_WARP)
         return fail(SSA_EUNSUPPORTED, "fast mode runs in the lane layout only");
@@ -299,6 +302,8 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
         layout = (tl::lane_f64_smem_bytes(m->L, 1) <= (size_t)smem_optin) ? SSA_LAYOUT_LANE : SSA_LAYOUT_WARP;
     if (moments && layout != SSA_LAYOUT_LANE)
         return fail(SSA_EUNSUPPORTED, "sweep moments are accumulated by the lane layout only");
+    if (o.mode == SSA_MODE_CLE && layout != SSA_LAYOUT_LANE)
+        return fail(SSA_EUNSUPPORTED, "network too large for the lane layout, which Langevin increments need");
     auto smem_of = [&](int w) {
         return layout == SSA_LAYOUT_LANE ? tl::lane_f64_smem_bytes(m->L, w) : tl::warp_f64_smem_bytes(m->L, w);
     };

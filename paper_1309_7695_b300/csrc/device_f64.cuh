@@ -545,6 +545,31 @@ __device__ __forceinline__ long long ptrs_draw(double lam, uint64_t seed, uint32
     return -1;
 }
 
+// Langevin increment for a leap mean lam >= kCleMinMean (SSA_MODE_CLE; the
+// chemical Langevin equation, Gillespie 2000): the Poisson count replaced
+// by its normal approximation rounded to the nearest count,
+// k = max(0, floor(lam + sqrt(lam) z + 1/2)), z ~ N(0,1) by Marsaglia's
+// polar method with one stream block per try (v = 2u - 1, accepted when
+// 0 < s = v1^2 + v2^2 < 1, z = v1 sqrt(-2 ln s / s)).  Returns -1 after
+// kPtrsMaxIters rejected tries, kCountLimit + 1 above the count limit.
+constexpr double kCleMinMean = 1000.0;
+__device__ __forceinline__ long long normal_leap(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+{
+    for (uint32_t it = 0; it < (uint32_t)kPtrsMaxIters; ++it) {
+        const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
+        const double v1 = 2.0 * u01(w.x, w.y) - 1.0;
+        const double v2 = 2.0 * u01(w.z, w.w) - 1.0;
+        const double s = v1 * v1 + v2 * v2;
+        if (!(s < 1.0) || !(s > 0.0)) continue;
+        const double z = v1 * sqrt((-2.0 * dlog(s)) / s);
+        const double k = floor((lam + sqrt(lam) * z) + 0.5);
+        if (k < 0.0) return 0;
+        if (k > (double)kCountLimit) return kCountLimit + 1;
+        return (long long)k;
+    }
+    return -1;
+}
+
 // k ~ Poisson(lam) on the stream (sim, attempt, reaction j): 0 for lam <= 0,
 // kCountLimit + 1 for a mean at or above 2^40, inversion below 10, PTRS
 // from 10 on.

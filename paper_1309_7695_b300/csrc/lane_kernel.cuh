@@ -603,7 +603,10 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             }
                             for (int q = lane; q < n_ptrs; q += 32) {
                                 const int j = w.jl[M + q];
-                                const long long kj = Arith::ptrs(__longlong_as_double(w.k[j]), GL.seed, sL, attL, (uint32_t)j);
+                                const double lam = __longlong_as_double(w.k[j]);
+                                const long long kj = (A.mode == SSA_MODE_CLE && f64::nn_ge(lam, f64::kCleMinMean))
+                                                         ? f64::normal_leap(lam, GL.seed, sL, attL, (uint32_t)j)
+                                                         : Arith::ptrs(lam, GL.seed, sL, attL, (uint32_t)j);
                                 if (kj < 0) krej = 1;
                                 else if (kj > f64::kCountLimit) kover = 1;
                                 w.k[j] = kj;
