@@ -151,7 +151,10 @@ int ssa_model_info(ssa_model_t model, int32_t *n_species, int32_t *n_reactions);
  * Simulation r uses the random stream of global index sim_offset + r
  * (sim_offset + n_sims <= 2^32).  Returns as soon as the launch is queued;
  * the function allocates a small stream-ordered work counter and frees it
- * on the same stream. */
+ * on the same stream.  The first launch on each device also copies the
+ * logarithm table (6 KB, built on the host) into device memory with a
+ * synchronous copy, so make one launch on a device before capturing
+ * launches into a CUDA graph. */
 int ssa_simulate_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
                      const double *params, const int32_t *x0, double t_end,
                      const double *sample_times, int32_t n_samples, uint64_t seed,
