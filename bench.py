@@ -160,7 +160,7 @@ def run_reference(args):
 
     batch = make_batch(0)
     o = oracle.default_opts(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"], max_attempts=WORKLOAD["max_attempts"])
-    per_step = 256
+    per_step = 2048   # the same sample as cpu_baseline: every 32nd simulation of the batch
     stride = batch.n_sims // per_step
     rows = np.arange(0, batch.n_sims, stride)[:per_step]
     for w in range(args.warmup):
