@@ -61,3 +61,23 @@ def test_host_side_validation_without_gpu(libpath):
     with pytest.raises(abi.SsaError) as e:
         abi.Model(bad)
     assert e.value.code == abi.SSA_EINVAL
+
+
+def test_new_entry_points_reject_null_handles_without_gpu(libpath):
+    # argument checks of the sweep-moments, RRE and multi-network entry points
+    # run before any CUDA call, so they answer on a machine without a GPU
+    import ctypes
+
+    from paper_1309_7695_b300 import abi
+    lib = abi.lib()
+    o = abi.ssa_default_options()
+    rc = lib.ssa_simulate_moments_dev(None, 4, 0, None, None, 1.0, None, 2, 0, ctypes.byref(o), None, None, None, None)
+    assert rc == abi.SSA_EINVAL and b"model" in lib.ssa_last_error()
+    rc = lib.ssa_integrate_rre_dev(None, 4, None, None, None, 2, 1e-8, 1e-8, 100, None, None, None)
+    assert rc == abi.SSA_EINVAL
+    rc = lib.ssa_simulate_multi_dev(-1, None, ctypes.byref(o), None)
+    assert rc == abi.SSA_EINVAL
+    o.mode = 7
+    rc = lib.ssa_simulate_multi_dev(1, (abi.Group * 1)(), ctypes.byref(o), None)
+    assert rc == abi.SSA_EINVAL and b"mode" in lib.ssa_last_error()
+    assert abi.SSA_MODE_CLE == 2
