@@ -195,3 +195,22 @@ def test_sample_moments_match_numpy_and_exact_cases(oracle_lib):
     one = np.array([[[5]]], dtype=np.int32)
     m, v = oracle_lib.sample_moments(one)
     assert m[0, 0] == 5.0 and v[0, 0] == 0.0
+
+
+def test_log_at_table_grid_points_is_nearly_correctly_rounded(oracle_lib):
+    # at x = F_j = 1 + j/256 (and its binary scalings) the table method reduces
+    # to e ln 2 + (hi_j + lo_j) with r = 0, so the result shows the table entry
+    # itself: it must be within 0.51 ulp of the 50-digit logarithm
+    getcontext().prec = 50
+    xs = []
+    for j in range(257):
+        F = 1.0 + j / 256.0
+        xs += [F, F / 2.0, F * 8.0, F * 2.0 ** -40]
+    xs = np.array(xs)
+    got = oracle_lib.log_array(xs)
+    for x, g in zip(xs, got):
+        exact = Decimal(float(x)).ln()
+        if exact == 0:
+            assert g == 0.0
+            continue
+        assert abs(Decimal(float(g)) - exact) <= Decimal("0.51") * Decimal(math.ulp(float(exact))), (x, g)
