@@ -11,6 +11,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -19,12 +20,93 @@
 namespace tl {
 namespace f64 {
 
+// Every function below is __host__ __device__: on the device it compiles to
+// the intrinsics named here, on the host to portable code with the same
+// values (a test builds them for the CPU and compares them with the oracle).
+#define TL_HD __host__ __device__ __forceinline__
+
+namespace bits {
+TL_HD long long d2ll(double x)
+{
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    long long r;
+    memcpy(&r, &x, sizeof r);
+    return r;
+#endif
+}
+TL_HD double ll2d(long long v)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(v);
+#else
+    double r;
+    memcpy(&r, &v, sizeof r);
+    return r;
+#endif
+}
+TL_HD unsigned f2u(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    unsigned r;
+    memcpy(&r, &x, sizeof r);
+    return r;
+#endif
+}
+TL_HD float u2f(unsigned v)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(v);
+#else
+    float r;
+    memcpy(&r, &v, sizeof r);
+    return r;
+#endif
+}
+TL_HD int clzll(long long v)
+{
+#ifdef __CUDA_ARCH__
+    return __clzll(v);
+#else
+    return v == 0 ? 64 : __builtin_clzll((unsigned long long)v);
+#endif
+}
+TL_HD uint32_t umulhi(uint32_t a, uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+TL_HD double ull2d_rn(unsigned long long v)
+{
+#ifdef __CUDA_ARCH__
+    return __ull2double_rn(v);
+#else
+    return (double)v;
+#endif
+}
+TL_HD float d2f_rn(double v)
+{
+#ifdef __CUDA_ARCH__
+    return __double2float_rn(v);
+#else
+    return (float)v;
+#endif
+}
+}  // namespace bits
+
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds; each round
 // multiplies counter words 0 and 2 by the two round constants, mixes the
 // high halves with words 1 and 3 and the key, and the key advances by the
 // two Weyl increments between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+TL_HD uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -32,15 +114,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = bits::umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = bits::umulhi(0xCD9E8D57u, c.z);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     }
     return c;
 }
 
 // Stream block (sim, attempt, purpose<<24 | j, block) under key = seed.
-__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t purpose,
+TL_HD uint4 draw(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t purpose,
                                       uint32_t j, uint32_t block)
 {
     return philox4x32_10(make_uint4(sim, attempt, (purpose << 24) | j, block), (uint32_t)seed,
@@ -51,82 +133,82 @@ __device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t sim, uint32_t atte
 // (2m + 1) * 2^-53.  It is exact in double, so it is assembled from integer
 // bits here: the odd 53-bit integer 2m+1 is normalised with a leading-zero
 // count and given the matching exponent.
-__device__ __forceinline__ double u01(uint32_t w0, uint32_t w1)
+TL_HD double u01(uint32_t w0, uint32_t w1)
 {
     const uint64_t m = ((((uint64_t)w0) << 32) | (uint64_t)w1) >> 12;
     const uint64_t n = 2 * m + 1;                   // odd, < 2^53
-    const int lz = __clzll((long long)n);           // >= 11
+    const int lz = bits::clzll((long long)n);           // >= 11
     const uint64_t mant = (n << (lz - 11)) & 0x000FFFFFFFFFFFFFull;
     const uint64_t expo = (uint64_t)(1033 - lz);    // value = n * 2^-53
-    return __longlong_as_double((long long)((expo << 52) | mant));
+    return bits::ll2d((long long)((expo << 52) | mant));
 }
 
 // ------------------------------------------- exact bit-level helpers
 // For doubles that are never negative and never -0.0 (propensities, their
 // sums, times), IEEE order equals the order of the bit patterns read as
 // signed 64-bit integers, so these comparisons run on the integer pipe.
-__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
-__device__ __forceinline__ bool nn_ge(double a, double b) { return dbits(a) >= dbits(b); }
-__device__ __forceinline__ bool nn_gt(double a, double b) { return dbits(a) > dbits(b); }
-__device__ __forceinline__ bool nn_pos(double a) { return dbits(a) > 0; }
+TL_HD long long dbits(double v) { return bits::d2ll(v); }
+TL_HD bool nn_ge(double a, double b) { return dbits(a) >= dbits(b); }
+TL_HD bool nn_gt(double a, double b) { return dbits(a) > dbits(b); }
+TL_HD bool nn_pos(double a) { return dbits(a) > 0; }
 
 // Exact conversion of a count 0 <= v < 2^53 to double, assembled from bits
 // (normalise with a leading-zero count; no rounding can occur).  Larger
 // values use the round-to-nearest conversion.
-__device__ __forceinline__ double u53_to_double(unsigned long long v)
+TL_HD double u53_to_double(unsigned long long v)
 {
     if (v == 0) return 0.0;
-    if (v >= (1ull << 53)) return __ull2double_rn(v);
-    const int p = 63 - __clzll((long long)v);                       // v in [2^p, 2^(p+1))
+    if (v >= (1ull << 53)) return bits::ull2d_rn(v);
+    const int p = 63 - bits::clzll((long long)v);                       // v in [2^p, 2^(p+1))
     const unsigned long long frac = (v << (52 - p)) & 0x000FFFFFFFFFFFFFull;
-    return __longlong_as_double((long long)(((unsigned long long)(1023 + p) << 52) | frac));
+    return bits::ll2d((long long)(((unsigned long long)(1023 + p) << 52) | frac));
 }
-__device__ __forceinline__ double count_to_double(int x) { return u53_to_double((unsigned long long)(unsigned)x); }
+TL_HD double count_to_double(int x) { return u53_to_double((unsigned long long)(unsigned)x); }
 // Conversions between FP32 and FP64 assembled from bits on the integer pipe
 // (on this GPU a conversion instruction costs as much as an FP64 add).
 // Both give the IEEE result: float -> double is exact, double -> float
 // rounds to nearest even.  Values outside the normal float range (zero
 // aside) take the conversion instruction.
-__device__ __forceinline__ double f32_to_f64(float f)
+TL_HD double f32_to_f64(float f)
 {
-    const unsigned u = __float_as_uint(f);
+    const unsigned u = bits::f2u(f);
     const unsigned e = (u >> 23) & 0xffu;
     const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    if ((u << 1) == 0) return __longlong_as_double((long long)sign);   // +-0
+    if ((u << 1) == 0) return bits::ll2d((long long)sign);   // +-0
     if (e == 0 || e == 255) return (double)f;
-    return __longlong_as_double(
+    return bits::ll2d(
         (long long)(sign | ((unsigned long long)(e + (1023 - 127)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
 
-__device__ __forceinline__ float f64_to_f32(double d)
+TL_HD float f64_to_f32(double d)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned long long b = (unsigned long long)bits::d2ll(d);
     const unsigned sign = (unsigned)(b >> 63) << 31;
-    if ((b << 1) == 0) return __uint_as_float(sign);   // +-0
+    if ((b << 1) == 0) return bits::u2f(sign);   // +-0
     const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    if (e < -126 || e > 127) return __double2float_rn(d);
+    if (e < -126 || e > 127) return bits::d2f_rn(d);
     const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
     const unsigned m23 = (unsigned)(mant >> 29);
     const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
     unsigned r = ((unsigned)(e + 127) << 23) | m23;
     if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) r += 1;   // a carry moves into the exponent
-    return __uint_as_float(sign | r);
+    return bits::u2f(sign | r);
 }
 
 // +0 + a for a propensity a (>= +0, or -0 from a -0 rate): the canonical
 // sums start from +0, and adding the first term to +0 only clears the sign
 // of a zero, so the first term is taken with its sign bit cleared (integer
 // pipe) instead of being added.
-__device__ __forceinline__ double first_term(double a)
+TL_HD double first_term(double a)
 {
-    return __longlong_as_double(__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll);
+    return bits::ll2d(bits::d2ll(a) & 0x7FFFFFFFFFFFFFFFll);
 }
 
 // Exact conversion of a small signed integer (|v| < 2^31), from bits.
-__device__ __forceinline__ double small_to_double(int v)
+TL_HD double small_to_double(int v)
 {
     const double m = u53_to_double((unsigned long long)(v < 0 ? -(long long)v : (long long)v));
-    return v < 0 ? __longlong_as_double(__double_as_longlong(m) | (long long)0x8000000000000000ull) : m;
+    return v < 0 ? bits::ll2d(bits::d2ll(m) | (long long)0x8000000000000000ull) : m;
 }
 
 // ------------------------------------------------------ log, exp, log k!
@@ -209,6 +291,22 @@ inline void build(double *tab)
 // device code every unit that evaluates dlog holds its own).
 static __device__ double g_log_tab[3 * kLogTableN];
 
+// Entry i of the table: the device copy in device code, a host copy built
+// by the same builder in host code.
+TL_HD double log_tab(int i)
+{
+#ifdef __CUDA_ARCH__
+    return __ldg(&g_log_tab[i]);
+#else
+    static const double *tab = [] {
+        static double t[3 * kLogTableN];
+        logtab::build(t);
+        return (const double *)t;
+    }();
+    return tab[i];
+#endif
+}
+
 // Upload this unit's table to the current device, once per device (the
 // first launch on a device does it; it allocates nothing).
 static inline cudaError_t ensure_log_table()
@@ -241,26 +339,26 @@ static inline cudaError_t ensure_log_table()
 // relative.  e LN2_HI is exact; its sum with the table's high part keeps its
 // rounding error (Fast2Sum), and the low parts and ln(1 + r) are added after.
 // F and e as doubles are assembled from bits (exact, off the FP64 unit).
-__device__ __forceinline__ double dlog(double x)
+TL_HD double dlog(double x)
 {
-    long long bits = __double_as_longlong(x);
+    long long bits = bits::d2ll(x);
     int biased = (int)((bits >> 52) & 0x7ff);
     int adj = 0;
     if (biased == 0) {
         x = x * 0x1p54;
-        bits = __double_as_longlong(x);
+        bits = bits::d2ll(x);
         biased = (int)((bits >> 52) & 0x7ff);
         adj = -54;
     }
     int e = biased - 1023 + adj;
     const unsigned long long mant = (unsigned long long)bits & 0x000FFFFFFFFFFFFFull;
     const int j = (int)((mant + (1ull << 43)) >> 44);   // nearest 1/256 step, 0..256
-    const double m = __longlong_as_double((long long)(mant | 0x3FF0000000000000ull));
-    const double F = __longlong_as_double(j < 256 ? (long long)(0x3FF0000000000000ull | ((unsigned long long)j << 44))
+    const double m = bits::ll2d((long long)(mant | 0x3FF0000000000000ull));
+    const double F = bits::ll2d(j < 256 ? (long long)(0x3FF0000000000000ull | ((unsigned long long)j << 44))
                                                   : (long long)0x4000000000000000ull);
     if (j > 106) e = e + 1;
     const double f = m - F;
-    const double r = f * __ldg(&g_log_tab[j]);
+    const double r = f * log_tab(j);
     double p = -1.0 / 6.0;
     p = p * r + 1.0 / 5.0;
     p = p * r - 1.0 / 4.0;
@@ -269,19 +367,19 @@ __device__ __forceinline__ double dlog(double x)
     const double q = r + (r * r) * p;
     const double de = small_to_double(e);
     const double a = de * TL_LN2_HI;
-    const double ghi = __ldg(&g_log_tab[kLogTableN + j]);
+    const double ghi = log_tab(kLogTableN + j);
     const double hi = a + ghi;
     const double err = ghi - (hi - a);
-    const double lo = ((de * TL_LN2_LO + __ldg(&g_log_tab[2 * kLogTableN + j])) + err) + q;
+    const double lo = ((de * TL_LN2_LO + log_tab(2 * kLogTableN + j)) + err) + q;
     return hi + lo;
 }
 
 // e^x: n = floor(x/ln2 + 1/2), r = (x - n LN2_HI) - n LN2_LO, e^r by the
 // Taylor polynomial through r^13 in Horner form, then scaled by 2^n.
-__device__ __forceinline__ double dexp(double x)
+TL_HD double dexp(double x)
 {
     if (x != x) return x;
-    if (x > 709.0) return __longlong_as_double(0x7FF0000000000000ll);
+    if (x > 709.0) return bits::ll2d(0x7FF0000000000000ll);
     if (x < -745.0) return 0.0;
     const double n = floor(x * TL_INV_LN2 + 0.5);
     const double r = (x - n * TL_LN2_HI) - n * TL_LN2_LO;
@@ -304,12 +402,12 @@ __device__ __forceinline__ double dexp(double x)
         p = p * 0x1p-60;
         ni += 60;
     }
-    return p * __longlong_as_double((long long)((uint64_t)(ni + 1023) << 52));
+    return p * bits::ll2d((long long)((uint64_t)(ni + 1023) << 52));
 }
 
 // ln k!: exact product then ln for k < 10; Stirling's series through the
 // k^-13 term for k >= 10.
-__device__ __forceinline__ double dlnfact(long long k)
+TL_HD double dlnfact(long long k)
 {
     if (k < 10) {
         double f = 1.0;
@@ -340,7 +438,7 @@ constexpr int kInvTable = kInversionCap + 2;
 
 // The inversion draw of reaction j uses the first word pair of block 0 of
 // its stream.
-__device__ __forceinline__ double inversion_uniform(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+TL_HD double inversion_uniform(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
 {
     const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, 0);
     return u01(w.x, w.y);
@@ -354,7 +452,7 @@ __device__ __forceinline__ double inversion_uniform(uint64_t seed, uint32_t sim,
 // formed before the current one is tested, so the multiply chain of p and
 // the add chain of F overlap; u, F and p are positive, so the comparisons
 // run on their bit patterns (same order as the IEEE comparison).
-__device__ __forceinline__ long long inversion_draw(double lam, double u, const double *__restrict__ inv)
+TL_HD long long inversion_draw(double lam, double u, const double *__restrict__ inv)
 {
     double p = dexp(-lam);
     double F = p;
@@ -379,7 +477,7 @@ __device__ __forceinline__ long long inversion_draw(double lam, double u, const 
 // since k ln(k/lam) = 2k atanh(v) and k - lam = v (k + lam) (the saddle-point
 // form of Loader, "Fast and accurate computation of binomial probabilities",
 // 2000); every term there is small, so no precision is lost.
-__device__ __forceinline__ float log_pmf_f32(float k, float lam)
+TL_HD float log_pmf_f32(float k, float lam)
 {
     if (k < 10.0f) {
         float f = 1.0f;
@@ -427,7 +525,7 @@ __device__ __forceinline__ float log_pmf_f32(float k, float lam)
 // comparison is within the margin (or after 40 terms): then the FP64 search
 // decides.  The FP64 search's early stop (a term below the rounding of F)
 // happens only for u within 1e-15 of 1, which is always within the margin.
-__device__ __forceinline__ int inversion_certain(double lam, double u)
+TL_HD int inversion_certain(double lam, double u)
 {
     const float lf = f64_to_f32(lam);
     const float uf = f64_to_f32(u);
@@ -450,7 +548,7 @@ __device__ __forceinline__ int inversion_certain(double lam, double u)
 // all); the right side by log_pmf_f32 (deviance form; the rounding of lam
 // to FP32 moves it by at most |k - lam| 2^-23).  Returns +1 (accept), -1
 // (reject) or 0 (within the margin, or lam >= 2^22: decide in FP64).
-__device__ __forceinline__ int ptrs_accept_certain(double lam, long long k, double V, double us, double a, double b)
+TL_HD int ptrs_accept_certain(double lam, long long k, double V, double us, double a, double b)
 {
     if (!(lam < 0x1p22)) return 0;
     const float lf = f64_to_f32(lam), kf = (float)k, af = f64_to_f32(a), bf = f64_to_f32(b);
@@ -468,18 +566,18 @@ __device__ __forceinline__ int ptrs_accept_certain(double lam, long long k, doub
 }
 
 // K * 2^-53 for an integer 0 < K < 2^53, exactly, from bits.
-__device__ __forceinline__ double scaled53(unsigned long long K)
+TL_HD double scaled53(unsigned long long K)
 {
-    return __longlong_as_double(__double_as_longlong(u53_to_double(K)) - (53ll << 52));
+    return bits::ll2d(bits::d2ll(u53_to_double(K)) - (53ll << 52));
 }
 
 // floor(x) of a finite double as an integer, from bits (exact; the same
 // value as the rounding instruction followed by a conversion).  |x| >= 2^62
 // is returned as +-2^62: callers only test such values for sign and for
 // exceeding the count limit.
-__device__ __forceinline__ long long floor_to_ll(double x)
+TL_HD long long floor_to_ll(double x)
 {
-    const long long bits = __double_as_longlong(x);
+    const long long bits = bits::d2ll(x);
     const int e = (int)((bits >> 52) & 0x7ff) - 1023;   // x = 1.f * 2^e
     const bool neg = bits < 0;
     if (e < 0) return (neg && (bits << 1) != 0) ? -1 : 0;   // |x| < 1
@@ -506,12 +604,12 @@ __device__ __forceinline__ long long floor_to_ll(double x)
 // the same result: U = u - 1/2 and us = 1/2 - |U| are integer multiples of
 // 2^-53 (u = (2m+1) 2^-53), 2a doubles a positive number, and the floor, its
 // conversion and the comparisons of non-negative values use bit patterns.
-__device__ __forceinline__ long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
 {
     const double slam = sqrt(lam);
     const double b = 0.931 + 2.53 * slam;
     const double a = -0.059 + 0.02483 * b;                                      // > 0 for lam >= 10
-    const double two_a = __longlong_as_double(__double_as_longlong(a) + (1ll << 52));   // 2a, exactly
+    const double two_a = bits::ll2d(bits::d2ll(a) + (1ll << 52));   // 2a, exactly
     const double vr = 0.9277 - 3.6224 / (b - 2.0);                              // > 0 for lam >= 10
     // ln lam and 1/alpha serve only the acceptance test after the squeeze,
     // so they are formed on first use (same values, shorter common path)
@@ -553,7 +651,7 @@ __device__ __forceinline__ long long ptrs_draw(double lam, uint64_t seed, uint32
 // 0 < s = v1^2 + v2^2 < 1, z = v1 sqrt(-2 ln s / s)).  Returns -1 after
 // kPtrsMaxIters rejected tries, kCountLimit + 1 above the count limit.
 constexpr double kCleMinMean = 1000.0;
-__device__ __forceinline__ long long normal_leap(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+TL_HD long long normal_leap(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
 {
     for (uint32_t it = 0; it < (uint32_t)kPtrsMaxIters; ++it) {
         const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
@@ -573,7 +671,7 @@ __device__ __forceinline__ long long normal_leap(double lam, uint64_t seed, uint
 // k ~ Poisson(lam) on the stream (sim, attempt, reaction j): 0 for lam <= 0,
 // kCountLimit + 1 for a mean at or above 2^40, inversion below 10, PTRS
 // from 10 on.
-__device__ __forceinline__ long long poisson(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
+TL_HD long long poisson(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
                                              uint32_t j, const double *__restrict__ inv)
 {
     if (!(lam > 0.0)) return 0;
