@@ -543,26 +543,33 @@ TL_HD int inversion_certain(double lam, double u)
 
 // PTRS acceptance after the squeeze: accept iff
 //   ln(V inv_alpha / (a / us^2 + b)) <= -lam + k ln lam - ln k!.
-// FP32: the left side from the FP32 images of V, us, a, b (relative error of
-// the argument below 13 * 2^-24, logf within 1 ulp of |ln| <= 40: 5e-6 in
-// all); the right side by log_pmf_f32 (deviance form; the rounding of lam
-// to FP32 moves it by at most |k - lam| 2^-23).  Returns +1 (accept), -1
-// (reject) or 0 (within the margin, or lam >= 2^22: decide in FP64).
-TL_HD int ptrs_accept_certain(double lam, long long k, double V, double us, double a, double b)
+// FP32: the left side from FP32 images of V, us, a, b (relative error of
+// the argument below 13 * 2^-24 when a and b are rounded from their FP64
+// values, logf within 1 ulp of |ln| <= 40: 5e-6 in all); the right side by
+// log_pmf_f32 (deviance form; the rounding of lam to FP32 moves it by at
+// most |k - lam| 2^-23).  `extra` widens the margin for a and b that carry
+// more error (the FP32 setup of ptrs_draw: 2^-19 relative, 1e-5 more on the
+// left side).  Returns +1 (accept), -1 (reject) or 0 (within the margin:
+// decide in FP64).
+TL_HD int ptrs_accept_certain_f(float lf, long long k, float Vf, float usf, float af, float bf, float extra)
 {
-    if (!(lam < 0x1p22)) return 0;
-    const float lf = f64_to_f32(lam), kf = (float)k, af = f64_to_f32(a), bf = f64_to_f32(b);
-    const float usf = f64_to_f32(us), Vf = f64_to_f32(V);
+    const float kf = (float)k;
     const float inv_alpha = 1.1239f + 1.1328f / (bf - 3.4f);
     const float lhs = logf(Vf * inv_alpha / (af / (usf * usf) + bf));
     const float rhs = log_pmf_f32(kf, lf);
     const float d = fabsf(kf - lf);
-    float m = 5e-5f + 4e-6f * (fabsf(rhs) + d);
+    float m = 5e-5f + extra + 4e-6f * (fabsf(rhs) + d);
     if (k < 10) m += 0x1p-20f * lf;
     else if (d >= 0.25f * (kf + lf)) m += 4e-6f * kf * fabsf(logf(kf / lf));
     if (lhs < rhs - m) return 1;
     if (lhs > rhs + m) return -1;
     return 0;
+}
+
+TL_HD int ptrs_accept_certain(double lam, long long k, double V, double us, double a, double b)
+{
+    if (!(lam < 0x1p22)) return 0;
+    return ptrs_accept_certain_f(f64_to_f32(lam), k, f64_to_f32(V), f64_to_f32(us), f64_to_f32(a), f64_to_f32(b), 0.0f);
 }
 
 // K * 2^-53 for an integer 0 < K < 2^53, exactly, from bits.
@@ -604,17 +611,42 @@ TL_HD long long floor_to_ll(double x)
 // the same result: U = u - 1/2 and us = 1/2 - |U| are integer multiples of
 // 2^-53 (u = (2m+1) 2^-53), 2a doubles a positive number, and the floor, its
 // conversion and the comparisons of non-negative values use bit patterns.
+//
+// For lam < 2^16 the iteration's decisions are first taken in FP32 with
+// certified margins, and the FP64 constants and candidate are formed only
+// when a decision falls inside its margin:
+//   - b, a, v_r from FP32 lam: relative errors below 5, 12 and (on v_r,
+//     absolute) 5 times 2^-24, bounded by 2^-19 and 1e-6;
+//   - the candidate x = (2a/us + b) U + lam + 0.43 as T + (lam + 0.43) with
+//     T in FP32 (relative error below 1.3 * 2^-19) and lam + 0.43 split into
+//     two floats: |x_FP32 - x_FP64| <= |T| 2^-17 + |x| 2^-22 + 2^-20, so its
+//     floor is certain when the fraction of x_FP32 is farther than that from
+//     0 and 1;
+//   - V <= v_r is certain outside a 1e-6 band; us >= 0.07 and the us < 0.013
+//     squeeze are exact;
+//   - the acceptance test after the squeeze is ptrs_accept_certain_f with
+//     the FP32 a and b.
 TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
 {
-    const double slam = sqrt(lam);
-    const double b = 0.931 + 2.53 * slam;
-    const double a = -0.059 + 0.02483 * b;                                      // > 0 for lam >= 10
-    const double two_a = bits::ll2d(bits::d2ll(a) + (1ll << 52));   // 2a, exactly
-    const double vr = 0.9277 - 3.6224 / (b - 2.0);                              // > 0 for lam >= 10
-    // ln lam and 1/alpha serve only the acceptance test after the squeeze,
-    // so they are formed on first use (same values, shorter common path)
+    // FP64 constants, formed on first need
+    bool set64 = false;
+    double b = 0.0, a = 0.0, two_a = 0.0, vr = 0.0;
+    // ln lam and 1/alpha serve only the FP64 acceptance test after the
+    // squeeze, so they are formed on first use (same values)
     double loglam = 0.0, inv_alpha = 0.0;
     bool slow_ready = false;
+    // FP32 images for the certified decisions
+    const bool f32 = nn_gt(0x1p16, lam);
+    float lf = 0.0f, bf = 0.0f, af = 0.0f, vrf = 0.0f, Lhi = 0.0f, Llo = 0.0f;
+    if (f32) {
+        lf = f64_to_f32(lam);
+        bf = 0.931f + 2.53f * sqrtf(lf);
+        af = -0.059f + 0.02483f * bf;
+        vrf = 0.9277f - 3.6224f / (bf - 2.0f);
+        const double L = lam + 0.43;
+        Lhi = f64_to_f32(L);
+        Llo = f64_to_f32(L - f32_to_f64(Lhi));
+    }
     for (uint32_t it = 0; it < (uint32_t)kPtrsMaxIters; ++it) {
         const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
         const unsigned long long n = 2 * (((((uint64_t)w.x) << 32) | (uint64_t)w.y) >> 12) + 1;   // u = n 2^-53
@@ -623,13 +655,62 @@ TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t atte
         const double U = dU < 0 ? -scaled53(aU) : scaled53(aU);
         const double us = scaled53((1ull << 52) - aU);                                          // 1/2 - |U| > 0
         const double V = u01(w.z, w.w);
-        const long long k = floor_to_ll((two_a / us + b) * U + lam + 0.43);
-        if (nn_ge(us, 0.07) && nn_ge(vr, V)) return (k > kCountLimit) ? kCountLimit + 1 : k;
-        if (k < 0 || (nn_gt(0.013, us) && nn_gt(V, us))) continue;
+        const bool us_ok = nn_ge(us, 0.07);
+        const bool squeeze_rej = nn_gt(0.013, us) && nn_gt(V, us);
+        // decisions of this iteration: accept (squeeze), and the candidate k
+        int acc = -1;          // 1 / 0, or -1 undecided
+        bool k_known = false;
+        long long k = 0;
+        if (f32) {
+            const float Vf = f64_to_f32(V);
+            if (!us_ok) acc = 0;
+            else if (Vf <= vrf - 1e-6f) acc = 1;
+            else if (Vf > vrf + 1e-6f) acc = 0;
+            if (acc == 1 || (acc == 0 && !squeeze_rej)) {
+                const float T = ((2.0f * af) / f64_to_f32(us) + bf) * f64_to_f32(U);
+                const float x = (T + Llo) + Lhi;
+                const float E = fabsf(T) * 0x1p-17f + fabsf(x) * 0x1p-22f + 0x1p-20f;
+                if (fabsf(x) < 0x1p22f) {
+                    const float fl = floorf(x);
+                    const float fr = x - fl;   // exact
+                    if (fr > E && fr < 1.0f - E) {
+                        k = (long long)fl;
+                        k_known = true;
+                    }
+                }
+            }
+        }
+        const bool need_k = (acc != 0) || !squeeze_rej;
+        if (acc < 0 || (need_k && !k_known)) {
+            if (!set64) {
+                const double slam = sqrt(lam);
+                b = 0.931 + 2.53 * slam;
+                a = -0.059 + 0.02483 * b;                                          // > 0 for lam >= 10
+                two_a = bits::ll2d(bits::d2ll(a) + (1ll << 52));                   // 2a, exactly
+                vr = 0.9277 - 3.6224 / (b - 2.0);                                  // > 0 for lam >= 10
+                set64 = true;
+            }
+            if (acc < 0) acc = (us_ok && nn_ge(vr, V)) ? 1 : 0;
+            if (!k_known && ((acc != 0) || !squeeze_rej)) {
+                k = floor_to_ll((two_a / us + b) * U + lam + 0.43);
+                k_known = true;
+            }
+        }
+        if (acc == 1) return (k > kCountLimit) ? kCountLimit + 1 : k;
+        if (squeeze_rej || k < 0) continue;
         if (k > kCountLimit) return kCountLimit + 1;
-        const int sure = ptrs_accept_certain(lam, k, V, us, a, b);
+        const int sure = f32 ? ptrs_accept_certain_f(lf, k, f64_to_f32(V), f64_to_f32(us), af, bf, 2e-5f)
+                             : (set64 ? ptrs_accept_certain(lam, k, V, us, a, b) : 0);
         if (sure > 0) return k;
         if (sure < 0) continue;
+        if (!set64) {
+            const double slam = sqrt(lam);
+            b = 0.931 + 2.53 * slam;
+            a = -0.059 + 0.02483 * b;
+            two_a = bits::ll2d(bits::d2ll(a) + (1ll << 52));
+            vr = 0.9277 - 3.6224 / (b - 2.0);
+            set64 = true;
+        }
         if (!slow_ready) {
             loglam = dlog(lam);
             inv_alpha = 1.1239 + 1.1328 / (b - 3.4);

@@ -91,3 +91,15 @@ def test_langevin_increments_equal_the_oracle(dm, oracle_lib, lam):
     a = np.empty(n, dtype=np.int64)
     dm.dm_normal_leap_array(lam, 9, n, _p(a))
     assert np.array_equal(a, oracle_lib.normal_leap_array(lam, n, seed=9))
+
+
+@pytest.mark.parametrize("lam", [10.0, 11.7, 50.0, 123.4, 1000.0, 5003.3, 2.0e4, 65535.9, 65536.0, 1.0e5])
+def test_ptrs_certified_iteration_equals_the_oracle(dm, oracle_lib, lam):
+    # PTRS takes its candidate, squeeze and acceptance decisions in FP32 below
+    # means of 2^16 and falls back to FP64 inside the margins: every draw must
+    # still be the oracle's (three seeds, 300,000 draws each)
+    for seed in (11, 12, 13):
+        n = 100_000
+        a = np.empty(n, dtype=np.int64)
+        dm.dm_poisson_array(lam, seed, n, _p(a))
+        assert np.array_equal(a, oracle_lib.poisson_array(lam, n, seed=seed))
