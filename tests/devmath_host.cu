@@ -71,3 +71,26 @@ void dm_normal_leap_array(double lam, uint64_t seed, int64_t n, int64_t *out)
     for (int64_t i = 0; i < n; ++i) out[i] = f64::normal_leap(lam, seed, (uint32_t)i, 1u, 0u);
 }
 }
+
+extern "C" {
+void dm_f64_to_f32_array(const double *x, float *y, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = f64::f64_to_f32(x[i]);
+}
+void dm_f32_to_f64_array(const float *x, double *y, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = f64::f32_to_f64(x[i]);
+}
+void dm_floor_array(const double *x, int64_t *y, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = f64::floor_to_ll(x[i]);
+}
+void dm_u53_array(const uint64_t *v, double *y, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = f64::u53_to_double(v[i]);
+}
+void dm_small_array(const int32_t *v, double *y, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = f64::small_to_double(v[i]);
+}
+}

@@ -36,6 +36,8 @@ def dm(tmp_path_factory):
     L.dm_poisson_array.argtypes = [f64, u64, i64, vp]
     L.dm_poisson_certified_array.argtypes = [f64, u64, i64, vp, vp]
     L.dm_normal_leap_array.argtypes = [f64, u64, i64, vp]
+    for name in ("dm_f64_to_f32_array", "dm_f32_to_f64_array", "dm_floor_array", "dm_u53_array", "dm_small_array"):
+        getattr(L, name).argtypes = [vp, vp, i64]
     return L
 
 
@@ -103,3 +105,43 @@ def test_ptrs_certified_iteration_equals_the_oracle(dm, oracle_lib, lam):
         a = np.empty(n, dtype=np.int64)
         dm.dm_poisson_array(lam, seed, n, _p(a))
         assert np.array_equal(a, oracle_lib.poisson_array(lam, n, seed=seed))
+
+
+def test_bit_assembled_conversions_equal_ieee(dm):
+    # the kernels replace conversion instructions by integer bit assembly;
+    # numpy's IEEE conversions are the reference (round to nearest even)
+    rng = np.random.default_rng(83)
+    bitsd = rng.integers(0, 2**63, 500_000, dtype=np.int64) | (rng.integers(0, 2, 500_000, dtype=np.int64) << 63)
+    x = bitsd.view(np.float64)
+    x = x[np.isfinite(x)]
+    edge = np.array([0.0, -0.0, 1.0, -1.0, 3.4028234663852886e38, 3.4028235677973366e38, 1.1754943508222875e-38,
+                     1.1754942106924411e-38, 2.0**-149, 1.5 * 2.0**-149, 1e-300, 1e300, 0.1, 1 + 2.0**-24,
+                     1 + 3 * 2.0**-24, 1 + 2.0**-24 + 2.0**-50])
+    x = np.concatenate([x, edge, np.exp(rng.uniform(-100, 100, 200_000)) * rng.choice([-1.0, 1.0], 200_000)])
+    y = np.empty(len(x), dtype=np.float32)
+    dm.dm_f64_to_f32_array(_p(x), _p(y), len(x))
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    assert np.array_equal(y.view(np.uint32), ref.view(np.uint32))
+    f = rng.integers(0, 2**32, 500_000, dtype=np.uint64).astype(np.uint32).view(np.float32)
+    f = f[np.isfinite(f)]
+    yd = np.empty(len(f))
+    dm.dm_f32_to_f64_array(_p(f), _p(yd), len(f))
+    assert np.array_equal(yd.view(np.int64), f.astype(np.float64).view(np.int64))
+
+
+def test_bit_assembled_floor_and_integer_conversions(dm):
+    rng = np.random.default_rng(84)
+    x = np.concatenate([rng.uniform(-1e6, 1e6, 300_000), rng.uniform(-3, 3, 100_000), np.round(rng.uniform(-1e9, 1e9, 10_000)),
+                        np.array([-0.0, 0.0, -0.5, 0.5, -1.0, 2.0**52 + 1, -(2.0**52) - 1, 2.0**61, -(2.0**61)])])
+    y = np.empty(len(x), dtype=np.int64)
+    dm.dm_floor_array(_p(x), _p(y), len(x))
+    assert np.array_equal(y, np.floor(x).astype(np.int64))
+    v = np.concatenate([rng.integers(0, 2**53, 200_000, dtype=np.uint64), np.array([0, 1, 2**52, 2**53 - 1], dtype=np.uint64)])
+    yu = np.empty(len(v))
+    dm.dm_u53_array(_p(v), _p(yu), len(v))
+    assert np.array_equal(yu, v.astype(np.float64))
+    s = np.concatenate([rng.integers(-2**31 + 1, 2**31, 200_000), np.array([0, 1, -1, 2, -2, 127, -128])]).astype(np.int32)
+    ys = np.empty(len(s))
+    dm.dm_small_array(_p(s), _p(ys), len(s))
+    assert np.array_equal(ys, s.astype(np.float64))
