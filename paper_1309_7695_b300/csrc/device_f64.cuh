@@ -572,6 +572,20 @@ TL_HD int ptrs_accept_certain(double lam, long long k, double V, double us, doub
     return ptrs_accept_certain_f(f64_to_f32(lam), k, f64_to_f32(V), f64_to_f32(us), f64_to_f32(a), f64_to_f32(b), 0.0f);
 }
 
+// The leap's tau'' = -ln(u)/a0c matters only if it can be the smallest of
+// tau'', tau' and the gap to the next sample time.  True when an FP32 lower
+// bound of it (logf within 1 ulp, u and a0c rounded to FP32, 1e-4 slack,
+// 2^-20 absolute for u near 1) lies above m = min(tau', gap) > 0, so that the
+// canonical comparisons certainly find no critical firing.  Requires a0c > 0
+// and u >= 2^-126 (FP32-normal); the uniforms here are all >= 2^-53.
+TL_HD bool tau2_surely_later(double u, double a0c, double m)
+{
+    const float a0cf = f64_to_f32(a0c);
+    const float Ef = -logf(f64_to_f32(u));
+    const float lo = fmaxf(Ef * 0.9999f - 0x1p-20f, 0.0f) / (a0cf * 1.0001f);
+    return a0cf >= 0x1p-126f && lo <= 0x1p127f && nn_gt(f32_to_f64(lo), m);
+}
+
 // K * 2^-53 for an integer 0 < K < 2^53, exactly, from bits.
 TL_HD double scaled53(unsigned long long K)
 {

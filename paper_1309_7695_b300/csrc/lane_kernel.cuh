@@ -518,20 +518,14 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             Arith::uniforms(GL.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
                             const double t_stop = (ksL < S) ? tnL : t_end;
                             const double delta = t_stop - tL;
-                            // tau'' = -ln(u)/a0c matters only if it can be the smallest of
-                            // tau'' , tau' and delta.  An FP32 lower bound (logf within 1 ulp,
-                            // u and a0c rounded to FP32, 1e-4 slack, 2^-20 absolute for u near
-                            // 1) above min(tau', delta) settles "no critical firing", and +inf
-                            // then stands in for tau'' in the comparisons below.
+                            // tau'' matters only if it can be the smallest of tau'', tau' and
+                            // delta; when a certified FP32 lower bound says it cannot, +inf
+                            // stands in for it in the comparisons below
                             double tau2 = kInf;
                             if (f64::nn_pos(a0c)) {
-                                const float a0cf = f64::f64_to_f32(a0c);
-                                const float Ef = -logf(f64::f64_to_f32(u_tau));
-                                const float lo = fmaxf(Ef * 0.9999f - 0x1p-20f, 0.0f) / (a0cf * 1.0001f);
                                 const double m = f64::nn_ge(delta, tau1) ? tau1 : delta;
-                                const bool surely_later = a0cf >= 0x1p-126f && lo <= 0x1p127f &&
-                                                          f64::nn_gt(f64::f32_to_f64(lo), m);
-                                if (!surely_later) tau2 = Arith::tau_of(Arith::neglog(u_tau), a0c);
+                                if (!f64::tau2_surely_later(u_tau, a0c, m))
+                                    tau2 = Arith::tau_of(Arith::neglog(u_tau), a0c);
                             }
                             double tau;
                             int jc = -1;

@@ -94,3 +94,10 @@ void dm_small_array(const int32_t *v, double *y, int64_t n)
     for (int64_t i = 0; i < n; ++i) y[i] = f64::small_to_double(v[i]);
 }
 }
+
+extern "C" {
+void dm_tau2_screen_array(const double *u, const double *a0c, const double *m, uint8_t *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = f64::tau2_surely_later(u[i], a0c[i], m[i]) ? 1 : 0;
+}
+}

@@ -38,6 +38,7 @@ def dm(tmp_path_factory):
     L.dm_normal_leap_array.argtypes = [f64, u64, i64, vp]
     for name in ("dm_f64_to_f32_array", "dm_f32_to_f64_array", "dm_floor_array", "dm_u53_array", "dm_small_array"):
         getattr(L, name).argtypes = [vp, vp, i64]
+    L.dm_tau2_screen_array.argtypes = [vp, vp, vp, vp, i64]
     return L
 
 
@@ -145,3 +146,37 @@ def test_bit_assembled_floor_and_integer_conversions(dm):
     ys = np.empty(len(s))
     dm.dm_small_array(_p(s), _p(ys), len(s))
     assert np.array_equal(ys, s.astype(np.float64))
+
+
+def test_tau2_screen_never_hides_a_critical_firing(dm, oracle_lib):
+    # the leap drops tau'' = -ln(u)/a0c (Eq. 12's time to the next critical
+    # firing) only when the FP32 screen says it exceeds m = min(tau', gap);
+    # then the oracle's FP64 tau'' must exceed m too, or a critical firing the
+    # oracle makes would be lost.  m is placed at and around the exact tau''.
+    rng = np.random.default_rng(85)
+    n = 400_000
+    u = np.concatenate([rng.random(n // 4), 1 - rng.random(n // 4) * 2.0**-rng.integers(20, 53, n // 4),
+                        np.exp(-rng.uniform(0, 740, n // 4)), rng.random(n // 4) * 2.0**-rng.integers(0, 127, n // 4)])
+    # the screen's domain: u >= 2^-126, since every uniform is (m + 1/2) 2^-52
+    assert oracle_lib.u01(0, 0) == 2.0**-53
+    u = np.clip(u, 2.0**-126, np.nextafter(1.0, 0.0))
+    a0c = np.exp(rng.uniform(-300, 300, n)) * rng.choice([1.0, 1e-10, 1e10], n)
+    E = -oracle_lib.log_array(u)
+    with np.errstate(over="ignore", under="ignore"):
+        tau2 = E / a0c
+    rel = np.concatenate([np.zeros(n // 4), rng.uniform(-1e-3, 1e-3, n // 4),
+                          rng.uniform(-1e-6, 1e-6, n // 4), rng.uniform(-0.5, 0.5, n // 4)])
+    with np.errstate(over="ignore", invalid="ignore"):
+        m = tau2 * (1 + rel)
+    m = np.where(rng.random(n) < 0.05, np.nextafter(tau2, 0.0), m)
+    ok = np.isfinite(m) & (m > 0) & np.isfinite(tau2)
+    u, a0c, m, tau2 = u[ok], a0c[ok], m[ok], tau2[ok]
+    out = np.empty(len(u), dtype=np.uint8)
+    dm.dm_tau2_screen_array(_p(u), _p(a0c), _p(m), _p(out), len(u))
+    later = out.astype(bool)
+    assert np.all(tau2[later] > m[later])
+    # and it settles most cases that are not close: tau'' above 1.01 m with a0c
+    # and tau'' in FP32 normal range and u not within 2^-18 of 1
+    clear = (tau2 > 1.01 * m) & (a0c > 1e-37) & (a0c < 1e37) & (tau2 < 1e37) & (u < 1 - 2.0**-18) & (tau2 > 1e-30)
+    assert clear.sum() > 5_000
+    assert later[clear].mean() > 0.999
