@@ -180,3 +180,21 @@ def test_tau2_screen_never_hides_a_critical_firing(dm, oracle_lib):
     clear = (tau2 > 1.01 * m) & (a0c > 1e-37) & (a0c < 1e37) & (tau2 < 1e37) & (u < 1 - 2.0**-18) & (tau2 > 1e-30)
     assert clear.sum() > 5_000
     assert later[clear].mean() > 0.999
+
+
+def test_philox_equals_the_oracle_on_1e9_words(oracle_lib, tmp_path):
+    # the engine's Philox and the oracle's, written separately from the
+    # published round function, agree word for word over 2.5e8 blocks
+    from oracle import build as oracle_build
+
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    lib = oracle_build.build()
+    exe = str(tmp_path / "philox_words_check")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-ffp-contract=off",
+                    "-I", os.path.join(ROOT, "include"), "-o", exe, os.path.join(ROOT, "tests", "philox_words_check.cu"),
+                    "-L", os.path.dirname(lib), "-loracle", "-Xlinker", "-rpath=" + os.path.dirname(lib)], check=True)
+    words, mismatches = (int(v) for v in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split())
+    assert words == 10**9
+    assert mismatches == 0

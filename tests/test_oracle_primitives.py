@@ -103,6 +103,33 @@ def test_exp_within_2ulp_of_libm(oracle_lib):
     assert oracle_lib.exp(0.0) == 1.0
 
 
+def test_log_exp_against_the_c_library_over_1e8_inputs(oracle_lib, tmp_path):
+    # the bound at scale, against glibc's ln and exp called from C: 10^8 ln
+    # inputs (every binade, (0,1) uniforms, near 1, [0.5, 2)), 10^8 exp inputs
+    # with normal results and 10^8 with subnormal ones.  exp stays within
+    # 1 ulp.  ln does too except in [1 - 2^-9, 1 - 2^-12), where the table
+    # value ln(F/2) ~ -2e-3 cancels against the polynomial in r = (m - F)/F,
+    # and r's rounding then reaches ~1.6 ulp of the result (2 ulp from glibc
+    # for ~3 inputs in a million there)
+    import shutil
+    import subprocess
+    from oracle import build as oracle_build
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lib = oracle_build.build()
+    exe = str(tmp_path / "ulp_check")
+    subprocess.run([gcc, "-O2", "-ffp-contract=off", "-o", exe, os.path.join(os.path.dirname(__file__), "oracle_ulp_check.c"),
+                    "-L", os.path.dirname(lib), "-loracle", "-Wl,-rpath," + os.path.dirname(lib), "-lm"], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    n, max_log, over_log, max_exp, over_exp, max_sub, over_sub = (int(v) for v in out)
+    assert n == 100_000_000
+    assert max_log <= 2 and over_log <= 20
+    assert max_exp <= 1 and over_exp == 0
+    assert max_sub <= 1 and over_sub == 0
+
+
 def test_lnfact_exact_small_and_stirling_large(oracle_lib):
     getcontext().prec = 60
     ks = np.array(list(range(0, 200)) + [500, 1000, 4096], dtype=np.int64)
