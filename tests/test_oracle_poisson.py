@@ -26,6 +26,32 @@ def test_poisson_pmf_chi_square(oracle_lib, lam, n):
     assert p > 1e-3, (lam, p)
 
 
+@pytest.mark.parametrize("lam", [0.1, 1.0, 9.99, 10.0, 30.0, 1000.0, 1e6])
+def test_poisson_chi_square_and_ks_on_1e7_draws(oracle_lib, lam):
+    # 10^7 draws per mean against the exact pmf (scipy): chi-square over the
+    # support (bins of 100 values at 10^6), and the largest gap between the
+    # empirical and the exact cdf, judged by the Kolmogorov law (conservative
+    # for a discrete law)
+    n = 10_000_000
+    k = oracle_lib.poisson_array(lam, n, seed=2024)
+    assert k.min() >= 0
+    lo, hi = int(k.min()), int(k.max())
+    support = np.arange(lo, hi + 1)
+    counts = np.bincount(k - lo, minlength=len(support)).astype(np.float64)
+    cdf = stats.poisson.cdf(support, lam)
+    d = np.max(np.abs(np.cumsum(counts) / n - cdf))
+    assert stats.kstwobign.sf(d * np.sqrt(n)) > 1e-3, (lam, d)
+    if lam >= 1e5:
+        edges = np.arange(lo, hi + 101, 100)
+        counts = np.add.reduceat(counts, edges[:-1] - lo)
+        probs = np.diff(stats.poisson.cdf(edges - 1, lam))
+    else:
+        probs = stats.poisson.pmf(support, lam)
+    probs[0] += stats.poisson.cdf(lo - 1, lam)
+    probs[-1] += stats.poisson.sf(support[-1] if lam < 1e5 else edges[-1] - 1, lam)
+    assert chi2_pvalue(counts, probs) > 1e-3, lam
+
+
 @pytest.mark.parametrize("lam", [0.3, 7.0, 12.0, 250.0, 1e6])
 def test_poisson_moments(oracle_lib, lam):
     n = 200_000
