@@ -107,14 +107,15 @@ def test_tiny_system_matches_exact_cme(name, net, rates, x0, mode):
 
 # ------------------------------------------- tau-leap at large counts
 
-@pytest.mark.parametrize("eps", [0.03, 0.01])
+@pytest.mark.parametrize("eps", [0.03, 0.01, 0.003])
 def test_isomerization_tau_leap_mean_follows_leap_recursion(eps):
     # A -> B with k = 1, A(0) = 1e4.  tau' = min(eps/k, eps^2 A/k) (g_A = 1,
     # mu = -kA, sigma^2 = kA) equals eps/k while A >= 1/eps, which holds here
     # throughout (A stays above 3000); the reaction is noncritical and
     # A_{n+1} = A_n - Poisson(k A_n tau), so E[A_n] = A0 (1 - eps)^n and
     # Var[A_{n+1}] = (1 - eps)^2 Var[A_n] + eps E[A_n].  Sample times are
-    # multiples of 0.3, an integer number of steps of eps.
+    # multiples of 0.3, an integer number of steps of eps.  At eps = 0.003
+    # the SSA-fallback threshold 10/a0 <= 2.5e-3 stays below tau'.
     times = [0.0, 0.3, 0.6, 0.9]
     reps = 4000
     s, st = run(inputs.isomerization(), [1.0], [10_000, 0], reps, 0.9, times, TAU, seed=5,
