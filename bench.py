@@ -317,6 +317,154 @@ def run_served(args):
     return 0
 
 
+def rre_fp64_ops_per_attempt(net):
+    """FP64 operations of one Dormand-Prince 5(4) attempt of one system.
+
+    Six right-hand sides (the seventh stage is the next step's first): the
+    mass-action rates (0 ops for order 0, 1 for X, 2 for X+Y, 3 for 2X) and,
+    per net-change entry, one product and one sum; the stage combinations
+    (3 + 5 + 7 + 9 + 11 ops per species, and 11 for the solution) and the
+    error norm (~20 per species, one division among them)."""
+    rate_ops = sum(0 if not r else (1 if len(r) == 1 and r[0][1] == 1 else (2 if len(r) == 2 else 3))
+                   for r in net.reactants)
+    nnz = int((net.stoichiometry() != 0).sum())
+    return 6 * (rate_ops + 2 * nnz) + 66 * net.n_species
+
+
+def _timed_launches(torch, launch, seeds, flush, stream):
+    """One launch per seed, L2 flushed before each, each timed alone with
+    CUDA events on the launching stream; returns the summed seconds."""
+    total = 0.0
+    for sd in seeds:
+        flush.fill_(sd & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launch(sd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / 1e3
+    return total
+
+
+def run_rre(args):
+    """Batched reaction-rate-equation integration (the deterministic mean-field
+    counterpart): the 32 x 64 random network's parameter sweep integrated by
+    Dormand-Prince 5(4) with a power-of-two step controller, one warp per
+    system, FP64 (bit-exact with the oracle's integration).  Reported:
+    integration attempts/s (accepted + rejected steps) and the FP64 roofline
+    position; the oracle's rate on a strided sample beside it."""
+    import torch
+
+    from paper_1309_7695_b300 import abi
+
+    dev = torch.device("cuda:0")
+    b = inputs.random_batch(32, 64, args.rre_sims, seed=0, t_end=args.rre_t_end, n_samples=args.rre_samples,
+                            network_seed=0)
+    net = b.network
+    n, N, S = b.n_sims, net.n_species, len(b.sample_times)
+    model = abi.Model(net)
+    p = torch.from_numpy(b.params).to(dev)
+    x = torch.from_numpy(b.x0).to(dev)
+    T = torch.from_numpy(b.sample_times).to(dev)
+    out = torch.empty((n, S, N), dtype=torch.float64, device=dev)
+    st = torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def launch(_):
+        abi.ssa_integrate_rre_dev(model, p, x, T, out, st, rtol=1e-8, atol=1e-8, max_steps=1_000_000, stream=stream)
+
+    _timed_launches(torch, launch, range(args.warmup), flush, stream)
+    clocks = ClockSampler(0)
+    clocks.start()
+    dt = _timed_launches(torch, launch, range(args.steps), flush, stream)
+    clk = clocks.stop()
+    s = st.cpu().numpy().view(abi.STATS_DTYPE).reshape(-1)
+    attempts = float(s["attempts"].sum()) * args.steps     # every launch integrates the same systems
+    accepted = float(s["leaps"].sum()) * args.steps
+    ops = attempts * rre_fp64_ops_per_attempt(net)
+    achieved = ops / dt
+    line = {"metric": "RRE integration attempts/s (Dormand-Prince 5(4), FP64, bit-exact with the oracle)",
+            "workload": "rre", "value": attempts / dt, "unit": "attempts/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "accepted_steps_per_s": accepted / dt, "systems_per_s": n * args.steps / dt,
+            "dtype": "f64", "data": "synthetic (seeded random network and parameter sweep)",
+            "status_ok": int((s["status"] == 0).sum()), "max_attempts_one_system": int(s["attempts"].max()),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
+                         "unit": "T FP64-op/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
+                         "ops_per_attempt": rre_fp64_ops_per_attempt(net),
+                         "peak_source": "nominal B300 FP64 1.25 TFLOP/s, a multiply-add counted once"},
+            "gpu_launches": args.steps, "clocks": clk,
+            "config": {"workload": f"RRE of a random mass-action network 32 species x 64 reactions, {n} parameter "
+                                   f"sets (rates logU[1e-4,1], x0 U{{0..1000}}), t_end={args.rre_t_end:g}, {S} sample "
+                                   f"times, rtol=atol=1e-8", "l2": "flushed before every launch"}}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        rows = np.arange(0, n, 16)
+        t0 = time.perf_counter()
+        _, ost = oracle.rre_simulate(net, b.params[rows], b.x0[rows], b.sample_times, rtol=1e-8, atol=1e-8,
+                                     max_steps=1_000_000)
+        odt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(ost["attempts"].sum()) / odt, "unit": "attempts/s",
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"every 16th system ({len(rows)} of {n})", "seconds": round(odt, 2)}
+    model.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cle(args):
+    """The Langevin leap against the Poisson leap on a workload where every
+    leap mean is large: birth-death 0 -> X (c = 2e5), X -> 0 (c = 1) from
+    X = 0 to t_end = 5 (stationary mean 2e5), FP64, one launch per mode,
+    same seeds.  Reported: leap attempts/s of each mode and their ratio."""
+    import torch
+
+    from paper_1309_7695_b300 import abi
+
+    dev = torch.device("cuda:0")
+    b = inputs.replicate_batch(inputs.birth_death(), [2e5, 1.0], [0], args.cle_sims, 5.0, 6)
+    n, N, S = b.n_sims, 1, len(b.sample_times)
+    model = abi.Model(b.network)
+    p = torch.from_numpy(b.params).to(dev)
+    x = torch.from_numpy(b.x0).to(dev)
+    T = torch.from_numpy(b.sample_times).to(dev)
+    out = torch.empty((n, S, N), dtype=torch.int32, device=dev)
+    st = torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, mode in (("langevin", abi.SSA_MODE_CLE), ("poisson", abi.SSA_MODE_TAU_LEAP)):
+        o = abi.ssa_default_options(mode=mode, layout=abi.SSA_LAYOUT_LANE, max_attempts=1 << 20)
+
+        def launch(sd):
+            abi.ssa_simulate_dev(model, p, x, b.t_end, T, out, st, seed=sd, opts=o, stream=stream)
+
+        _timed_launches(torch, launch, [300 + w for w in range(args.warmup)], flush, stream)
+        dt, leaps, ssa, fir = 0.0, 0.0, 0.0, 0.0
+        for k in range(args.steps):
+            dt += _timed_launches(torch, launch, [100 + k], flush, stream)
+            s = st.cpu().numpy().view(abi.STATS_DTYPE).reshape(-1)
+            leaps += float(s["leaps"].sum() + s["rejected"].sum())
+            ssa += float(s["ssa_steps"].sum())
+            fir += float(s["firings"].sum())
+        res[name] = {"leap_attempts_per_s": leaps / dt, "sim_steps_per_s": (leaps + ssa) / dt,
+                     "firings_per_s": fir / dt, "ms_per_step": dt * 1e3 / args.steps}
+    line = {"metric": "leap attempts/s, Langevin vs Poisson leap", "workload": "cle",
+            "value": res["langevin"]["leap_attempts_per_s"], "unit": "leap attempts/s",
+            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
+            "data": "synthetic", "langevin": res["langevin"], "poisson": res["poisson"],
+            "langevin_vs_poisson": res["langevin"]["leap_attempts_per_s"] / res["poisson"]["leap_attempts_per_s"],
+            "gpu_launches": 2 * args.steps,
+            "config": {"workload": f"birth-death 0->X (2e5), X->0 (1), X0=0, t_end=5, {S} sample times, "
+                                   f"{n} replicates, lane layout", "l2": "flushed before every launch"}}
+    model.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # FP64 peak: the nominal B300 FP64 rate, 1.25 TFLOP/s, as FP64 operations with
 # a multiply-add counted once (the unit of the algorithmic counts above)
 FP64_PEAK_OPS = 1.25e12 / 2
@@ -339,7 +487,11 @@ def main():
     # profiling / sweep knobs; the reported benchmark uses the defaults
     ap.add_argument("--sims", type=int, default=None, help="override the simulations per GPU (profiling)")
     ap.add_argument("--cap", type=int, default=None, help="override the per-simulation attempt cap (profiling)")
-    ap.add_argument("--workload", default="rand32x64", choices=["rand32x64", "hetero", "served"])
+    ap.add_argument("--workload", default="rand32x64", choices=["rand32x64", "hetero", "served", "rre", "cle"])
+    ap.add_argument("--rre-sims", type=int, default=4096)
+    ap.add_argument("--rre-t-end", type=float, default=10.0)
+    ap.add_argument("--rre-samples", type=int, default=11)
+    ap.add_argument("--cle-sims", type=int, default=16384)
     ap.add_argument("--hetero-sims", type=int, default=20000)
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--serve-networks", type=int, default=32)
@@ -356,6 +508,10 @@ def main():
         return run_hetero(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "rre":
+        return run_rre(args)
+    if args.workload == "cle":
+        return run_cle(args)
 
     import torch
     import torch.distributed as dist
