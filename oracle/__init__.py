@@ -47,9 +47,12 @@ _lib = None
 
 
 def lib():
+    """The oracle library.  ORACLE_LIBRARY, when set, names another build of
+    the oracle's source to load instead (the mutation test uses it to run
+    the pins against copies of the oracle with one planted mistake)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("ORACLE_LIBRARY") or _build.build()
         L = ctypes.CDLL(path)
         u32p = ctypes.POINTER(ctypes.c_uint32)
         L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]

@@ -15,14 +15,21 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
 
+FLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+         "-Wall", "-Wextra"]
+
+
+def compile_source(src: str, out: str) -> None:
+    """Compile one oracle source file into a shared library with the oracle's flags."""
+    subprocess.run(["gcc", *FLAGS, "-o", out, src], check=True)
+
+
 def build(force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-Wall", "-Wextra", "-o", tmp, SRC]
-    subprocess.run(cmd, check=True)
+    compile_source(SRC, tmp)
     os.replace(tmp, LIB)
     return LIB
 

@@ -169,6 +169,10 @@ def test_tau_prime_one_reaction_closed_forms():
     # a species that is only a product of noncritical reactions bounds nothing
     q = oracle.leap_quantities(abc, [c], [xa, xb, 10**6], o)
     assert q["tau1"] == pytest.approx(expect, rel=1e-14)
+    # the same with the counts swapped: now the second reactant binds, so it
+    # must be a member of I_rs as well
+    q = oracle.leap_quantities(abc, [c], [xb, xa, 0], o)
+    assert q["tau1"] == pytest.approx(expect, rel=1e-14)
     # birth-death at X = 0: the death reaction has a = 0 but is not critical,
     # so X is a reactant species of a noncritical reaction and bounds the
     # step through the birth flux: tau' = min(1/k, 1/k) with bound 1.
@@ -187,6 +191,34 @@ def test_critical_set_uses_net_change():
     q = oracle.leap_quantities(net, [1.0, 1.0], [1, 0], o)
     assert list(q["crit"]) == [False, False]     # a_j = 0: never critical
     assert q["a0"] == 0.0
+    # the threshold itself (CGP 2005): critical iff L < n_c, so L = n_c is not
+    q = oracle.leap_quantities(net, [1.0, 1.0], [20, 0], o)
+    assert list(q["crit"]) == [False, False]     # L = 20 and 10
+    q = oracle.leap_quantities(net, [1.0, 1.0], [19, 0], o)
+    assert list(q["crit"]) == [False, True]      # L = 19 and 9
+    iso = inputs.isomerization()
+    assert not oracle.leap_quantities(iso, [1.0], [10, 0], o)["crit"][0]
+    assert oracle.leap_quantities(iso, [1.0], [9, 0], o)["crit"][0]
+    q = oracle.leap_quantities(iso, [1.0], [9, 0], oracle.default_opts(n_c=9))
+    assert not q["crit"][0]
+
+
+def test_critical_reactions_fire_at_their_exact_rate_beside_leaps():
+    # A -> 0 with A(0) = 8 < n_c is critical throughout, beside B -> 0 with
+    # B(0) = 1e5, which leaps.  tau'' is redrawn from the critical total a0c at
+    # every step and, being exponential, is memoryless, so the critical firings
+    # form the exact SSA of A alone: A(t) ~ Binomial(8, e^{-t}) at every t,
+    # however many leaps of B happen meanwhile.
+    net = inputs.Network(2, [[(0, 1)], [(1, 1)]], [[], []])
+    times = [0.25, 0.5, 1.0, 2.0]
+    reps = 20_000
+    s, st = run(net, [1.0, 1.0], [8, 100_000], reps, 2.0, times, TAU, seed=9)
+    assert np.all(st["status"] == 0)
+    assert st["leaps"].mean() > 50          # B does leap
+    for q, t in enumerate(times):
+        counts = np.bincount(s[:, q, 0], minlength=9)
+        probs = stats.binom.pmf(np.arange(9), 8, math.exp(-t))
+        assert chi2_pvalue(counts, probs) > 1e-3, t
 
 
 def test_mean_field_limit():
