@@ -35,6 +35,9 @@ MUTANTS = [
     ("philox round multiplier", "(uint64_t)0xD2511F53u * (uint64_t)c0", "(uint64_t)0xD2511F55u * (uint64_t)c0"),
     ("philox key increment", "k0 += 0x9E3779B9u;", "k0 += 0x9E3779BBu;"),
     ("u01 offset", "return ((double)m + 0.5) * 0x1p-52;", "return ((double)m + 0.25) * 0x1p-52;"),
+    ("philox round count", "for (int round = 0; round < 10; ++round) {", "for (int round = 0; round < 9; ++round) {"),
+    ("philox output words swapped", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;"),
+    ("u01 keeps 53 bits", "| (uint64_t)w1) >> 12;", "| (uint64_t)w1) >> 11;"),
     # ln, exp, ln k!
     ("ln polynomial coefficient", "    p = p * r + 1.0 / 3.0;\n    p = p * r - 1.0 / 2.0;",
      "    p = p * r + 1.0 / 4.0;\n    p = p * r - 1.0 / 2.0;"),
@@ -43,6 +46,7 @@ MUTANTS = [
     ("exp Taylor coefficient", "p = p * r + 1.0 / 24.0;", "p = p * r + 1.0 / 25.0;"),
     ("exp reduction sign", "double r = (x - n * LN2_HI) - n * LN2_LO;", "double r = (x - n * LN2_HI) + n * LN2_LO;"),
     ("ln k! Stirling term sign", "ser = ser * r2 - 1.0 / 360.0;", "ser = ser * r2 + 1.0 / 360.0;"),
+    ("ln k! Stirling from k = 2", "    if (k < 10) {\n        double f = 1.0;", "    if (k < 2) {\n        double f = 1.0;"),
     ("ln k! exact product bound", "for (int64_t i = 2; i <= k; ++i) f = f * (double)i;",
      "for (int64_t i = 2; i < k; ++i) f = f * (double)i;"),
     # Poisson sampler
@@ -51,7 +55,10 @@ MUTANTS = [
      "double rhs = -lam + kd * loglam - oracle_lnfact((int64_t)kd + 1);"),
     ("PTRS log-pmf uses sqrt", "double rhs = -lam + kd * loglam - oracle_lnfact((int64_t)kd);",
      "double rhs = -lam + kd * slam - oracle_lnfact((int64_t)kd);"),
+    ("PTRS rejects k = 0", "if (kd < 0.0 || (us < 0.013 && V > us)) continue;",
+     "if (kd <= 0.0 || (us < 0.013 && V > us)) continue;"),
     # Langevin increment
+    ("Langevin threshold", "#define CLE_MIN_MEAN 1000.0", "#define CLE_MIN_MEAN 100.0"),
     ("polar method drops /s", "double z = v1 * sqrt((-2.0 * oracle_log(s)) / s);",
      "double z = v1 * sqrt(-2.0 * oracle_log(s));"),
     ("Langevin increment scale", "double k = floor((lam + sqrt(lam) * z) + 0.5);", "double k = floor((lam + lam * z) + 0.5);"),
@@ -68,6 +75,7 @@ MUTANTS = [
      "double t2 = bound / w->sig2[i];"),
     ("bound multiplies by g", "double bound = (o->eps * xd) / g;", "double bound = (o->eps * xd) * g;"),
     ("g of an X+Y reactant", "case 2: g = 2.0; break;", "case 2: g = 1.0; break;"),
+    ("g of a 2X reactant", "g = (x[i] >= 2) ? 2.0 + 1.0 / (xd - 1.0) : 2.0;", "g = (x[i] >= 2) ? 2.0 + 1.0 / xd : 2.0;"),
     ("second reactant left out of I_rs", "if (kind == 2) w->irs[m->r_sp1[j]] = 1;", ";"),
     # leap
     ("tau'' divides by a0", "double tau2 = (a0c > 0.0) ? -oracle_log(u_tau) / a0c : INFINITY;",
@@ -76,6 +84,7 @@ MUTANTS = [
     ("critical reaction never fires in a leap", "w->k[j] = (j == jc) ? 1 : 0; continue;", "w->k[j] = 0; continue;"),
     ("leap update ignores k", "w->xnew[m->nu_sp[e]] += w->k[j] * (int64_t)m->nu_val[e];",
      "w->xnew[m->nu_sp[e]] += (int64_t)m->nu_val[e];"),
+    ("a leap to zero counts as negative", "if (w->xnew[i] < 0) neg = 1;", "if (w->xnew[i] <= 0) neg = 1;"),
     ("SSA fallback threshold", "if (do_ssa || tau1 < o->ssa_factor / a0) {", "if (do_ssa || tau1 < o->ssa_factor * a0) {"),
     # exact SSA step
     ("SSA selection reuses the time uniform", "int jf = canon_select(w->a, M, levels, u2 * a0);",
@@ -87,6 +96,7 @@ MUTANTS = [
     ("selection keeps the left mass", "            target = target - left;\n", "\n"),
     # reaction-rate equations
     ("Dormand-Prince weight", "DP_B3 = 500.0 / 1113.0", "DP_B3 = 500.0 / 1112.0"),
+    ("Dormand-Prince FSAL derivative not carried", "{ x[i] = xn[i]; k[1][i] = k[7][i]; }", "{ x[i] = xn[i]; }"),
     ("mean-field 2X rate", "default: a[j] = c[j] * ((x[m->r_sp0[j]] * x[m->r_sp0[j]]) * 0.5); break;",
      "default: a[j] = c[j] * (x[m->r_sp0[j]] * x[m->r_sp0[j]]); break;"),
 ]
@@ -116,7 +126,7 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
         pytest.skip("gcc not available")
     src = open(SRC).read()
     for name, before, _ in MUTANTS:
-        assert src.count(before) >= 1, f"mutation site of '{name}' not found"
+        assert src.count(before) == 1, f"mutation site of '{name}' not found exactly once"
     workers = max(1, min(6, (os.cpu_count() or 2) // 2))
     with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
         results = list(ex.map(lambda i: _run_mutant(i, str(tmp_path)), range(len(MUTANTS))))
