@@ -19,9 +19,10 @@ FLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "
          "-Wall", "-Wextra"]
 
 
-def compile_source(src: str, out: str) -> None:
-    """Compile one oracle source file into a shared library with the oracle's flags."""
-    subprocess.run(["gcc", *FLAGS, "-o", out, src], check=True)
+def compile_source(src: str, out: str, extra=()) -> None:
+    """Compile one oracle source file into a shared library with the oracle's
+    flags (plus `extra`, e.g. sanitizer flags for a checking build)."""
+    subprocess.run(["gcc", *FLAGS, *extra, "-o", out, src], check=True)
 
 
 def build(force: bool = False) -> str:
