@@ -198,3 +198,21 @@ def test_philox_equals_the_oracle_on_1e9_words(oracle_lib, tmp_path):
     words, mismatches = (int(v) for v in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split())
     assert words == 10**9
     assert mismatches == 0
+
+
+def test_certified_routes_equal_the_oracle_at_random_means(dm, oracle_lib):
+    # the lane kernels' Poisson route (certified FP32 inversion, certified
+    # PTRS iteration and acceptance, FP64 inside the margins) at 650 random
+    # means from 1e-7 to 2^17, including the switch at 10 and the end of the
+    # FP32 iteration at 2^16, 20,000 draws each, on random seeds
+    rng = np.random.default_rng(86)
+    lams = np.concatenate([np.exp(rng.uniform(np.log(1e-7), np.log(10.0), 200)),
+                           np.exp(rng.uniform(np.log(10.0), np.log(2.0 ** 17), 400)),
+                           rng.uniform(9.9, 10.0, 25), 2.0 ** 16 + rng.uniform(-50, 50, 25)])
+    n = 20_000
+    for lam in lams:
+        seed = int(rng.integers(0, 2 ** 63))
+        a = np.empty(n, dtype=np.int64)
+        fb = ctypes.c_int64()
+        dm.dm_poisson_certified_array(float(lam), seed, n, _p(a), ctypes.byref(fb))
+        assert np.array_equal(a, oracle_lib.poisson_array(float(lam), n, seed=seed)), (lam, seed)
