@@ -52,12 +52,18 @@ EXPORTED = [
 
 
 class SsaError(RuntimeError):
+    """A call of the C ABI returned a negative SSA_E* code; ``code`` holds it
+    and the message is the library's ssa_last_error() text."""
+
     def __init__(self, code, msg):
         super().__init__(f"[{code}] {msg}")
         self.code = code
 
 
 class ModelDesc(ctypes.Structure):
+    """ssa_model_desc: species and reaction counts and the reactant and
+    product CSR arrays (int32)."""
+
     _fields_ = [
         ("n_species", ctypes.c_int32), ("n_reactions", ctypes.c_int32),
         ("react_ptr", ctypes.c_void_p), ("react_species", ctypes.c_void_p), ("react_coef", ctypes.c_void_p),
@@ -66,6 +72,9 @@ class ModelDesc(ctypes.Structure):
 
 
 class Group(ctypes.Structure):
+    """ssa_group: one (network, batch) entry of a persistent multi-network
+    launch; every pointer is a device pointer."""
+
     _fields_ = [
         ("model", ctypes.c_void_p), ("n_sims", ctypes.c_int64), ("sim_offset", ctypes.c_int64),
         ("params", ctypes.c_void_p), ("x0", ctypes.c_void_p), ("t_end", ctypes.c_double),
@@ -75,6 +84,9 @@ class Group(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
+    """ssa_options: method, precision, CGP constants (eps, n_c, the SSA
+    fallback factor and block), retry and attempt caps, and launch shape."""
+
     _fields_ = [
         ("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("eps", ctypes.c_double),
         ("n_c", ctypes.c_int32), ("ssa_block", ctypes.c_int32), ("ssa_factor", ctypes.c_double),
@@ -84,11 +96,17 @@ class Options(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
+    """ssa_server_config: HBM budget, stream slots, requests per launch and
+    the options applied to every request."""
+
     _fields_ = [("max_device_bytes", ctypes.c_int64), ("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("opts", Options)]
 
 
 class RequestInfo(ctypes.Structure):
+    """ssa_request_info: a request's state, the size of the launch it ran in,
+    and its submit / admit / done times (seconds since server creation)."""
+
     _fields_ = [("state", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("t_submit", ctypes.c_double),
                 ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
@@ -165,6 +183,9 @@ def _ptr(a):
 
 
 def ssa_default_options(**overrides) -> Options:
+    """The library's default options (tau-leaping, FP64 reference, eps 0.03,
+    n_c 10, SSA fallback 10/a0 with blocks of 100), with ``overrides`` set by
+    field name."""
     o = Options()
     lib().ssa_default_options(ctypes.byref(o))
     for k, v in overrides.items():
@@ -188,6 +209,7 @@ class Model:
         self.n_reactions = network.n_reactions
 
     def close(self):
+        """Free the model's device memory (ssa_free_model); idempotent."""
         if self.handle:
             lib().ssa_free_model(self.handle)
             self.handle = None
@@ -200,6 +222,8 @@ class Model:
 
 
 def ssa_load_model(network) -> Model:
+    """Validate ``network`` (an ``inputs.Network``) and upload it to the
+    current device."""
     return Model(network)
 
 
@@ -297,14 +321,18 @@ class Job:
         self.model, self.handle, self.n_sims, self.n_samples = model, handle, n_sims, n_samples
 
     def poll(self) -> int:
+        """SSA_JOB_RUNNING, SSA_JOB_DONE or SSA_JOB_FAILED, without blocking."""
         st = ctypes.c_int32()
         _check(lib().ssa_poll(self.handle, ctypes.byref(st)))
         return st.value
 
     def wait(self):
+        """Block until the job's work is complete."""
         _check(lib().ssa_wait(self.handle))
 
     def fetch(self, samples=None, stats=None):
+        """Wait, then copy samples [n][S][N] int32 and stats [n] to host arrays
+        (allocated when not given); returns (samples, stats)."""
         if samples is None:
             samples = np.empty((self.n_sims, self.n_samples, self.model.n_species), dtype=np.int32)
         if stats is None:
@@ -313,6 +341,7 @@ class Job:
         return samples, stats
 
     def release(self):
+        """Wait for the job and free everything it owns; idempotent."""
         if self.handle:
             _check(lib().ssa_release_job(self.handle))
             self.handle = None
@@ -325,6 +354,9 @@ class Job:
 
 
 def ssa_submit_batch(model: Model, params, x0, t_end, sample_times, seed=0, opts=None, stream=None) -> Job:
+    """Host-buffer job: params [n, M] float64, x0 [n, N] int32 and sample
+    times [S] are copied to device memory the job owns, and the simulation is
+    enqueued on ``stream`` (default: a stream of the job's own)."""
     params = np.ascontiguousarray(params, dtype=np.float64)
     x0 = np.ascontiguousarray(x0, dtype=np.int32)
     T = np.ascontiguousarray(sample_times, dtype=np.float64)
@@ -372,6 +404,8 @@ class Server:
         self._shapes = {}
 
     def submit(self, model, params, x0, t_end, sample_times, seed=0) -> int:
+        """Queue a request with host inputs (copied before returning); returns
+        its ticket.  Simulation r uses the stream (seed, r)."""
         params = np.ascontiguousarray(params, dtype=np.float64)
         x0 = np.ascontiguousarray(x0, dtype=np.int32)
         T = np.ascontiguousarray(sample_times, dtype=np.float64)
@@ -382,28 +416,35 @@ class Server:
         return t.value
 
     def poll(self, ticket) -> RequestInfo:
+        """The request's state and times, without blocking."""
         info = RequestInfo()
         _scheck(lib().ssa_server_poll(self.handle, int(ticket), ctypes.byref(info)))
         return info
 
     def wait(self, ticket) -> RequestInfo:
+        """Block until the request's launch has completed."""
         info = RequestInfo()
         _scheck(lib().ssa_server_wait(self.handle, int(ticket), ctypes.byref(info)))
         return info
 
     def fetch(self, ticket):
-        n, S, N = self._shapes.pop(ticket)
+        """Wait for the request, copy out (samples [n][S][N], stats [n]), free
+        its device memory and forget the ticket."""
+        n, S, N = self._shapes[ticket]
         samples = np.empty((n, S, N), dtype=np.int32)
         stats = np.empty(n, dtype=STATS_DTYPE)
         _scheck(lib().ssa_server_fetch(self.handle, int(ticket), _ptr(samples), _ptr(stats)))
+        del self._shapes[ticket]
         return samples, stats
 
     def stats(self):
+        """Launches issued, requests waiting for admission, admitted bytes."""
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _scheck(lib().ssa_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"launches": a.value, "queued": b.value, "device_bytes_in_use": c.value}
 
     def close(self):
+        """Finish queued and running requests and free everything; idempotent."""
         if self.handle:
             lib().ssa_server_destroy(self.handle)
             self.handle = None
