@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "OK", 1: "STEP_LIMIT", 2: "OVERFLOW", 3: "REJECT_LIMIT", 4: "
 
 
 class Opts(ctypes.Structure):
+    """oracle_opts: the method's options (mode, n_c, eps, SSA fallback factor and block, retry and attempt caps)."""
     _fields_ = [
         ("mode", ctypes.c_int32),
         ("n_c", ctypes.c_int32),
@@ -106,6 +107,7 @@ def _ptr(a):
 
 
 def philox(ctr, key):
+    """Philox4x32-10 (Salmon et al., SC'11) of a 4-word counter under a 2-word key."""
     c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
     k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
     o = (ctypes.c_uint32 * 4)()
@@ -114,26 +116,32 @@ def philox(ctr, key):
 
 
 def u01(w0, w1):
+    """The uniform (m + 1/2) 2^-52 of two Philox words, m their top 52 bits."""
     return lib().oracle_u01(w0, w1)
 
 
 def log(x):
+    """The canonical natural logarithm (Tang's table method)."""
     return lib().oracle_log(float(x))
 
 
 def exp(x):
+    """The canonical exponential (Cody-Waite reduction, Taylor polynomial)."""
     return lib().oracle_exp(float(x))
 
 
 def lnfact(k):
+    """The canonical ln k! (exact product below 10, Stirling's series above)."""
     return lib().oracle_lnfact(int(k))
 
 
 def poisson(lam, seed, sim, attempt, j):
+    """The canonical Poisson draw of reaction j at (simulation, attempt): inversion below 10, PTRS from 10."""
     return lib().oracle_poisson(float(lam), int(seed), int(sim), int(attempt), int(j))
 
 
 def log_array(x):
+    """log() of every element."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(x)
     lib().oracle_log_array(_ptr(x), _ptr(y), x.size)
@@ -141,6 +149,7 @@ def log_array(x):
 
 
 def exp_array(x):
+    """exp() of every element."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(x)
     lib().oracle_exp_array(_ptr(x), _ptr(y), x.size)
@@ -148,6 +157,7 @@ def exp_array(x):
 
 
 def lnfact_array(k):
+    """lnfact() of every element."""
     k = np.ascontiguousarray(k, dtype=np.int64)
     y = np.empty(k.shape, dtype=np.float64)
     lib().oracle_lnfact_array(_ptr(k), _ptr(y), k.size)
@@ -162,11 +172,13 @@ def poisson_array(lam, n, seed=0):
 
 
 def canon_sum(v):
+    """The canonical sum of v: 32 lane-striped slots, then the xor-butterfly tree."""
     v = np.ascontiguousarray(v, dtype=np.float64)
     return lib().oracle_canon_sum(_ptr(v), v.size)
 
 
 def canon_select(v, u):
+    """The canonical selection of an index with probability v[j] / canon_sum(v), given u in [0, 1)."""
     v = np.ascontiguousarray(v, dtype=np.float64)
     return int(lib().oracle_canon_select(_ptr(v), v.size, float(u)))
 
@@ -192,6 +204,7 @@ def leap_quantities(network, c, x, opts=None):
 
 def default_opts(mode=MODE_TAU_LEAP, eps=0.03, n_c=10, ssa_factor=10.0, ssa_block=100,
                  max_halvings=64, max_attempts=100_000_000) -> Opts:
+    """Options with the method's default constants (CGP 2006's suggested SSA fallback values)."""
     return Opts(mode, n_c, eps, ssa_factor, ssa_block, max_halvings, max_attempts)
 
 
@@ -235,6 +248,7 @@ def simulate_batch(batch, seed=0, opts=None, threads=0, rows=None):
 
 
 def num_threads() -> int:
+    """OpenMP threads the oracle's batch entry points use."""
     return int(lib().oracle_num_threads())
 
 

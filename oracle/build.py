@@ -26,6 +26,7 @@ def compile_source(src: str, out: str, extra=()) -> None:
 
 
 def build(force: bool = False) -> str:
+    """Compile liboracle.so unless it is newer than the source; returns its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB

@@ -17,11 +17,13 @@ from scipy.integrate import solve_ivp
 
 
 def integrate(network, rates, x0, times, rtol=1e-10, atol=1e-10):
+    """Mean-field trajectory X(t) at `times` ([len(times), N]) by scipy's RK45."""
     nu = network.stoichiometry().astype(np.float64)  # [N, M]
     reactants = network.reactants
     rates = np.asarray(rates, dtype=np.float64)
 
     def rhs(_t, x):
+        """dX/dt = nu a(X) with the mean-field rates."""
         a = np.empty(len(reactants))
         for j, row in enumerate(reactants):
             v = rates[j]

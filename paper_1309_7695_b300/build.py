@@ -34,6 +34,7 @@ UNITS = {
 
 
 def nvcc() -> str:
+    """Path of nvcc; the engine cannot be built without the CUDA toolkit."""
     path = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(path):
         raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libtauleap.so")
@@ -50,6 +51,7 @@ def _deps() -> list:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every unit for sm_103a and link libtauleap.so in the package, unless it is newer than every source; returns its path."""
     newest = max(os.path.getmtime(p) for p in _deps() + [os.path.abspath(__file__)])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB

@@ -35,6 +35,7 @@ class Network:
 
     @property
     def n_reactions(self) -> int:
+        """Number of reactions M."""
         return len(self.reactants)
 
     def csr(self) -> dict:
@@ -72,6 +73,7 @@ class Network:
         return nu
 
     def orders(self) -> np.ndarray:
+        """Reaction orders (sum of reactant coefficients), int32 [M]."""
         return np.asarray([sum(c for _, c in row) for row in self.reactants], dtype=np.int32)
 
 
@@ -87,6 +89,7 @@ class Batch:
 
     @property
     def n_sims(self) -> int:
+        """Number of simulations (parameter rows)."""
         return int(self.params.shape[0])
 
 
@@ -158,6 +161,7 @@ def random_network(n_species: int, n_reactions: int, seed: int) -> Network:
 # ------------------------------------------------------------ sweep inputs
 
 def log_uniform(rng: np.random.Generator, lo: float, hi: float, size) -> np.ndarray:
+    """Samples whose logarithm is uniform on [ln lo, ln hi]."""
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=size))
 
 
