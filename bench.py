@@ -134,21 +134,34 @@ def cpu_oracle_rate(batch, n_sample=2048, seed=1000):
     """Oracle firings/s and sim-steps/s on an evenly strided sample of the
     batch (every (n/n_sample)-th simulation, so heavy and light simulations
     appear in their batch proportions), all host cores, OpenMP over
-    simulations.  Rates are sample firings (steps) over sample wall time."""
+    simulations.  Rates are sample firings (steps) over sample wall time.
+    ``one_core`` times an eighth of that sample on one core and again on all
+    cores (firings per simulation are heavy-tailed, so only the same
+    simulations compare)."""
     import oracle
 
     o = oracle.default_opts(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"], max_attempts=WORKLOAD["max_attempts"])
+    cores = oracle.num_threads()
     stride = max(1, batch.n_sims // n_sample)
     rows = np.arange(0, batch.n_sims, stride)
-    t0 = time.perf_counter()
-    _, st = oracle.simulate_batch(batch, seed=seed, opts=o, rows=rows)
-    dt = time.perf_counter() - t0
-    fir = float(st["firings"].sum())
-    steps = float(st["leaps"].sum() + st["ssa_steps"].sum())
-    return {"value": fir / dt, "unit": "firings/s", "sim_steps_per_s": steps / dt,
-            "cores": oracle.num_threads(), "kind": "oracle", "seconds": round(dt, 2),
+
+    def timed(rs, threads):
+        t0 = time.perf_counter()
+        _, st = oracle.simulate_batch(batch, seed=seed, opts=o, rows=rs, threads=threads)
+        dt = time.perf_counter() - t0
+        return float(st["firings"].sum()) / dt, float(st["leaps"].sum() + st["ssa_steps"].sum()) / dt, dt
+
+    fir, steps, dt = timed(rows, cores)
+    rows1 = rows[::8]
+    f1, s1, d1 = timed(rows1, 1)
+    fa, sa, da = timed(rows1, cores)   # the same simulations on all cores (restores the thread count)
+    one_core = {"value": f1, "unit": "firings/s", "sim_steps_per_s": s1, "cores": 1, "seconds": round(d1, 2),
+                "all_cores_same_sample": fa, "speedup_all_cores": d1 / da,
+                "sample": f"every {stride * 8}th simulation ({len(rows1)} simulations)"}
+    return {"value": fir, "unit": "firings/s", "sim_steps_per_s": steps,
+            "cores": cores, "kind": "oracle", "seconds": round(dt, 2),
             "sample": f"every {stride}th of the {batch.n_sims} simulations ({len(rows)} simulations, "
-                      f"seed {seed}), OpenMP over simulations"}
+                      f"seed {seed}), OpenMP over simulations", "one_core": one_core}
 
 
 def run_reference(args):
