@@ -2,7 +2,7 @@
 
 tests/golden/rand32x64_65536_seed0_digests.txt holds the oracle's results of
 the 65,536-simulation random 32 x 64 sweep as block digests; the GPU test
-tests/test_zzz_full_batch_digest.py compares the engine's full batch with
+tests/test_zy_full_batch_digest.py compares the engine's full batch with
 them.  Here two blocks (one with a simulation that reaches the attempt cap,
 one without) are recomputed by the oracle alone, by their global simulation
 indices, so a change to the oracle that leaves the stored file stale fails on
