@@ -114,6 +114,9 @@ typedef struct {
     int64_t max_attempts; /* per-simulation cap on leap attempts + SSA steps (1e8) */
     int32_t block_warps;  /* warps per CTA, 0 = automatic */
     int32_t sims_per_warp; /* lane layout: lanes of a warp that own a simulation (1..32, 0 = 32) */
+    int32_t ctas_per_sm;   /* lane layout: resident CTAs per SM (0 = as many as fit); with fewer, the
+                              shared-memory carve-out is sized to them and the rest of each SM's
+                              on-chip memory serves as L1 cache for the rate constants */
 } ssa_options;
 
 /* Per-simulation counters and status (56 bytes). */
@@ -152,9 +155,11 @@ int ssa_model_info(ssa_model_t model, int32_t *n_species, int32_t *n_reactions);
  * (sim_offset + n_sims <= 2^32).  Returns as soon as the launch is queued;
  * the function allocates a small stream-ordered work counter and frees it
  * on the same stream.  The first launch on each device also copies the
- * logarithm table (6 KB, built on the host) into device memory with a
- * synchronous copy, so make one launch on a device before capturing
- * launches into a CUDA graph. */
+ * logarithm table (6 KB, built on the host) into device memory on `stream`
+ * and waits for that copy, so make one launch on a device before capturing
+ * launches into a CUDA graph.  The library keeps per-device state for the
+ * life of the process (that table); after a cudaDeviceReset the device must
+ * not be used through this library again. */
 int ssa_simulate_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
                      const double *params, const int32_t *x0, double t_end,
                      const double *sample_times, int32_t n_samples, uint64_t seed,
@@ -207,9 +212,11 @@ int ssa_integrate_rre_dev(ssa_model_t model, int64_t n_sims, const double *param
  * cudaFree or other allocating routine.  The one piece of scratch memory the
  * kernel needs, its 8-byte work counter, lives in a 256-byte static device
  * array that every GPU loading this library keeps until process exit; a
- * launch needing more scratch than that is rejected with SSA_EINVAL.  The
- * first call on each device looks up the array's device address, so make
- * that first call before any stream capture.  All calls share the array: the
+ * launch needing more scratch than that is rejected with SSA_EINVAL.  Each
+ * call looks up the array's device address on the model's device (this
+ * allocates nothing); the first call on a device also uploads the logarithm
+ * table as ssa_simulate_dev does, so make that first call before any stream
+ * capture.  All calls share the array: the
  * counter is cleared on `stream` before each launch, and calls whose work
  * overlaps on the GPU (different streams, or different host threads) race on
  * it and must be serialised by the caller.  The paper has no counterpart to
@@ -319,6 +326,23 @@ int ssa_server_stats(ssa_server_t srv, int64_t *launches, int64_t *queued, int64
 /* Finish queued and running requests, free everything. */
 int ssa_server_destroy(ssa_server_t srv);
 const char *ssa_server_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Measurement                                                           */
+/* ------------------------------------------------------------------ */
+/* Issue-rate microbenchmark of the current device, the denominator of the
+ * simulation kernels' roofline (they are bound by FP64 and FP32 instruction
+ * issue, not by memory bandwidth or tensor cores; the paper has no
+ * counterpart).  Launches, on `stream`, one full-device grid in which every
+ * thread runs 8 independent chains of 4,096 dependent adds (double, then
+ * float; no fused multiply-add), and one warp with a single dependent chain
+ * of double adds timed with the SM clock.  Writes the best of three timed
+ * launches as adds per second (*fp64_adds_per_s, *fp32_adds_per_s) and the
+ * SM cycles per dependent double add (*fp64_add_latency_cycles); any output
+ * pointer may be NULL.  Allocates and frees a few MB of stream-ordered
+ * scratch and synchronises `stream`.  SSA_ECUDA on any CUDA failure. */
+int ssa_measure_issue_rates(void *stream, double *fp64_adds_per_s, double *fp32_adds_per_s,
+                            double *fp64_add_latency_cycles);
 
 /* Message describing the last failed call on this thread ("" if none). */
 const char *ssa_last_error(void);

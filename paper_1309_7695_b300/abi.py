@@ -48,6 +48,7 @@ EXPORTED = [
     "ssa_release_job", "ssa_last_error", "ssa_abi_version",
     "ssa_server_default_config", "ssa_server_create", "ssa_server_submit", "ssa_server_poll", "ssa_server_wait",
     "ssa_server_fetch", "ssa_server_stats", "ssa_server_destroy", "ssa_server_last_error",
+    "ssa_measure_issue_rates",
 ]
 
 
@@ -91,7 +92,7 @@ class Options(ctypes.Structure):
         ("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("eps", ctypes.c_double),
         ("n_c", ctypes.c_int32), ("ssa_block", ctypes.c_int32), ("ssa_factor", ctypes.c_double),
         ("max_halvings", ctypes.c_int32), ("layout", ctypes.c_int32), ("max_attempts", ctypes.c_int64),
-        ("block_warps", ctypes.c_int32), ("sims_per_warp", ctypes.c_int32),
+        ("block_warps", ctypes.c_int32), ("sims_per_warp", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
     ]
 
 
@@ -161,6 +162,7 @@ def lib():
     L.ssa_server_destroy.argtypes = [vp]
     L.ssa_server_last_error.argtypes = []
     L.ssa_server_last_error.restype = ctypes.c_char_p
+    L.ssa_measure_issue_rates.argtypes = [vp, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(f64)]
     for name in EXPORTED:
         if name not in ("ssa_default_options", "ssa_last_error", "ssa_server_default_config",
                         "ssa_server_last_error"):
@@ -219,6 +221,21 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+def ssa_measure_issue_rates(stream=None) -> dict:
+    """The device's measured FP64 and FP32 add rates (adds/s over a full-device
+    grid) and the latency of one dependent FP64 add in SM cycles."""
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib().ssa_measure_issue_rates(ctypes.c_void_p(handle), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if rc != SSA_OK:
+        raise SsaError(rc, "issue-rate microbenchmark failed")
+    return {"fp64_adds_per_s": a.value, "fp32_adds_per_s": b.value, "fp64_add_latency_cycles": c.value}
 
 
 def ssa_load_model(network) -> Model:

@@ -30,6 +30,7 @@ UNITS = {
     "server.cu": [],
     "moments.cu": [],
     "kernel_rre.cu": ["-fmad=false"],
+    "peak.cu": ["-fmad=false"],
 }
 
 

@@ -42,6 +42,18 @@ struct DeviceGuard {
     }
 };
 
+// Shared-memory carve-out (percent of the SM's maximum) that holds `per_sm`
+// CTAs of `smem` bytes each plus the 1 KB the system reserves per CTA; the
+// rest of the on-chip memory is L1 cache.
+int smem_carveout_pct(int device, size_t smem, int per_sm)
+{
+    int max_sm = 0;
+    if (cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess || max_sm <= 0)
+        return -1;
+    const double need = (double)per_sm * (double)(smem + 1024);
+    return std::min(100, (int)std::ceil(100.0 * need / (double)max_sm));
+}
+
 }  // namespace
 
 struct ssa_model {
@@ -184,7 +196,8 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
     L.off_hor = L.off_tr_ent + nnz;
     L.off_dep_ptr = L.off_hor + N;
     L.off_dep_ent = L.off_dep_ptr + N + 1;
-    L.words = L.off_dep_ent + ndep;
+    L.off_cinfo = L.off_dep_ent + ndep;
+    L.words = L.off_cinfo + M;
     L.max_nu_len = max_nu_len;
     std::vector<int32_t> blob(L.words);
     std::copy(rinfo.begin(), rinfo.end(), blob.begin() + L.off_rinfo);
@@ -207,6 +220,18 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
         for (int v : dep_rows[i]) blob[L.off_dep_ent + pos++] = v;
     }
     blob[L.off_dep_ptr + N] = pos;
+    for (int j = 0; j < M; ++j) {
+        uint32_t ci = 0;
+        int slot = 0;
+        for (int v : nu_rows[j]) {
+            const int nv = (int)(signed char)(v & 0xff);
+            if (nv >= 0) continue;
+            // |nu| <= 2: only reactants are consumed, with coefficients <= 2
+            ci |= ((uint32_t)(v >> 8) | ((uint32_t)(-nv) << 14)) << (16 * slot);
+            ++slot;
+        }
+        blob[L.off_cinfo + j] = (int32_t)ci;
+    }
 
     auto *m = new ssa_model();
     m->L = L;
@@ -262,6 +287,7 @@ static int check_options(const ssa_options *o)
         return fail(SSA_EUNSUPPORTED, "unknown layout");
     if (o->block_warps < 0 || o->block_warps > 8) return fail(SSA_EINVAL, "block_warps must be in 0..8");
     if (o->sims_per_warp < 0 || o->sims_per_warp > 32) return fail(SSA_EINVAL, "sims_per_warp must be in 0..32");
+    if (o->ctas_per_sm < 0 || o->ctas_per_sm > 32) return fail(SSA_EINVAL, "ctas_per_sm must be in 0..32");
     return SSA_OK;
 }
 
@@ -315,7 +341,12 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     const int occ = layout == SSA_LAYOUT_LANE
                         ? (fast ? tl::lane_fast_occupancy(warps, smem) : tl::lane_ref_occupancy(warps, smem))
                         : tl::warp_ref_occupancy(warps, smem);
-    const int per_sm = std::max(1, occ);
+    int per_sm = std::max(1, occ);
+    int carveout = -1;   // the driver's default carve-out
+    if (layout == SSA_LAYOUT_LANE && o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) {
+        per_sm = o.ctas_per_sm;
+        carveout = smem_carveout_pct(m->device, smem, per_sm);
+    }
     const int spw = o.sims_per_warp > 0 ? o.sims_per_warp : 32;
     const long long sims_per_block = (long long)warps * (layout == SSA_LAYOUT_LANE ? spw : 1);
     const long long need_blocks = (n_sims + sims_per_block - 1) / sims_per_block;
@@ -348,8 +379,8 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     a.work_counter = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-        e = layout == SSA_LAYOUT_LANE ? (fast ? tl::launch_lane_fast(a, warps, grid, smem, s)
-                                              : tl::launch_lane_ref(a, warps, grid, smem, s))
+        e = layout == SSA_LAYOUT_LANE ? (fast ? tl::launch_lane_fast(a, warps, grid, smem, carveout, s)
+                                              : tl::launch_lane_ref(a, warps, grid, smem, carveout, s))
                                       : tl::launch_warp_ref(a, warps, grid, smem, s);
     cudaError_t e2 = counter_in ? cudaSuccess : cudaFreeAsync(counter, s);
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
@@ -370,29 +401,21 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
 // front) use the variant below, whose counter lives in this file-scope
 // array instead.  Every GPU that loads the library holds these 256 bytes
 // until the process exits.  In host code the symbol is only a host-side
-// stand-in, so its device address is looked up once per device with
-// cudaGetSymbolAddress and passed to the kernel.
+// stand-in, so its device address is looked up with cudaGetSymbolAddress
+// (with the model's device current) and passed to the kernel.
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[32];
 constexpr size_t kNoallocScratchBytes = sizeof(g_noalloc_scratch);
 constexpr size_t kNoallocCounterBytes = sizeof(unsigned long long);
 
-std::mutex g_noalloc_mutex;
-unsigned long long *g_noalloc_addr[256] = {nullptr};
-
-// Device address of the static scratch on the current device (looked up on
-// the first call per device).
-int noalloc_scratch(int device, unsigned long long **out)
+// Device address of the static scratch on the current device.  It is looked
+// up on every call (cheap, and it allocates nothing), so the address is never
+// one cached from before a cudaDeviceReset.
+int noalloc_scratch(unsigned long long **out)
 {
-    if (device < 0 || device >= 256) return fail(SSA_EUNSUPPORTED, "device ordinal above 255");
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
-            return fail(SSA_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        g_noalloc_addr[device] = static_cast<unsigned long long *>(p);
-    }
-    *out = g_noalloc_addr[device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    *out = static_cast<unsigned long long *>(p);
     return SSA_OK;
 }
 
@@ -634,6 +657,16 @@ int ssa_release_job(ssa_job_t j)
 int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_options *opts, void *stream)
 {
     g_error.clear();
+    return tl::simulate_multi_impl(n_groups, groups, opts, stream, nullptr, nullptr);
+}
+
+}  // extern "C"
+
+namespace tl {
+
+int simulate_multi_impl(int32_t n_groups, const ssa_group *groups, const ssa_options *opts, void *stream,
+                        unsigned long long *done_counts, volatile int32_t *done_flags)
+{
     if (n_groups < 0 || (n_groups > 0 && !groups)) return fail(SSA_EINVAL, "bad group list");
     if (n_groups == 0) return SSA_OK;
     ssa_options o;
@@ -670,6 +703,8 @@ int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_
         R.samples = G.samples;
         R.stats = G.stats;
         R.first = first;
+        R.done_count = done_counts ? done_counts + g : nullptr;
+        R.done_flag = done_flags ? done_flags + g : nullptr;
         first += G.n_sims;
         max_N = std::max(max_N, R.L.N);
         max_M = std::max(max_M, R.L.M);
@@ -687,9 +722,15 @@ int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_
     const size_t smem = tl::lane_multi_smem_bytes(max_N, max_M, warps);
     if (smem > (size_t)smem_optin) return fail(SSA_EUNSUPPORTED, "largest network too large for the workspace");
     const int occ = fast ? tl::lane_multi_fast_occupancy(warps, smem) : tl::lane_multi_ref_occupancy(warps, smem);
+    int per_sm = std::max(1, occ);
+    int carveout = -1;
+    if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) {
+        per_sm = o.ctas_per_sm;
+        carveout = smem_carveout_pct(device, smem, per_sm);
+    }
     const int spw = o.sims_per_warp > 0 ? o.sims_per_warp : 32;
     const long long per_block = (long long)warps * spw;
-    const int grid = (int)std::min<long long>((long long)std::max(1, occ) * sms, (first + per_block - 1) / per_block);
+    const int grid = (int)std::min<long long>((long long)per_sm * sms, (first + per_block - 1) / per_block);
 
     tl::SimArgs a{};
     a.n_groups = n_groups;
@@ -713,7 +754,8 @@ int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_
     if (e == cudaSuccess) {
         a.groups = static_cast<const tl::GroupArgs *>(d_table);
         a.work_counter = static_cast<unsigned long long *>(counter);
-        e = fast ? tl::launch_lane_multi_fast(a, warps, grid, smem, s) : tl::launch_lane_multi_ref(a, warps, grid, smem, s);
+        e = fast ? tl::launch_lane_multi_fast(a, warps, grid, smem, carveout, s)
+                 : tl::launch_lane_multi_ref(a, warps, grid, smem, carveout, s);
     }
     // the table copy is from pageable host memory, so the copy has been staged
     // before cudaMemcpyAsync returned and `table` may go out of scope
@@ -722,6 +764,10 @@ int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("multi launch: ") + cudaGetErrorString(e));
     return SSA_OK;
 }
+
+}  // namespace tl
+
+extern "C" {
 
 int ssa_simulate_dev_noalloc(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
                              const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
@@ -735,7 +781,7 @@ int ssa_simulate_dev_noalloc(ssa_model_t m, int64_t n_sims, int64_t sim_offset, 
     DeviceGuard g(m->device);
     if (!g.ok) return fail(SSA_ECUDA, "cannot select the model's device");
     unsigned long long *counter = nullptr;
-    int rc = noalloc_scratch(m->device, &counter);
+    int rc = noalloc_scratch(&counter);
     if (rc) return rc;
     return simulate_dev_impl(m, n_sims, sim_offset, params, x0, t_end, sample_times, n_samples, seed, opts,
                              samples, stats, stream, counter);

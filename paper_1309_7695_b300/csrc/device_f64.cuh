@@ -307,9 +307,15 @@ TL_HD double log_tab(int i)
 #endif
 }
 
-// Upload this unit's table to the current device, once per device (the
-// first launch on a device does it; it allocates nothing).
-static inline cudaError_t ensure_log_table()
+// Upload this unit's table to the current device, once per device: the
+// first launch on a device copies it on that launch's stream `s` and waits
+// for the copy to finish before marking the device done, so that launches
+// on any other stream afterwards read a complete table (a copy from pageable
+// memory may return before the data has reached the device, and is not
+// ordered with non-blocking streams).  It allocates nothing.  A
+// cudaDeviceReset discards the device copy; the library does not notice, so
+// a process that resets a device must not use the library on it again.
+static inline cudaError_t ensure_log_table(cudaStream_t s)
 {
     static std::mutex mu;
     static bool built = false, done[256] = {false};
@@ -324,7 +330,8 @@ static inline cudaError_t ensure_log_table()
         logtab::build(host);
         built = true;
     }
-    e = cudaMemcpyToSymbol(g_log_tab, host, sizeof host);
+    e = cudaMemcpyToSymbolAsync(g_log_tab, host, sizeof host, 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -640,15 +647,43 @@ TL_HD long long floor_to_ll(double x)
 //     squeeze are exact;
 //   - the acceptance test after the squeeze is ptrs_accept_certain_f with
 //     the FP32 a and b.
+// The FP64 pieces of a PTRS iteration, kept out of line: they run only when
+// a certified FP32 decision falls inside its margin (or for means of 2^16 and
+// above), so the common iteration stays a short instruction sequence.
+struct PtrsConsts {
+    double b, a, two_a, vr;
+};
+static __host__ __device__ __noinline__ PtrsConsts ptrs_consts64(double lam)
+{
+    PtrsConsts c;
+    const double slam = sqrt(lam);
+    c.b = 0.931 + 2.53 * slam;
+    c.a = -0.059 + 0.02483 * c.b;                          // > 0 for lam >= 10
+    c.two_a = bits::ll2d(bits::d2ll(c.a) + (1ll << 52));   // 2a, exactly
+    c.vr = 0.9277 - 3.6224 / (c.b - 2.0);                  // > 0 for lam >= 10
+    return c;
+}
+// The acceptance test after the squeeze, in FP64:
+//   ln(V inv_alpha / (a / us^2 + b)) <= -lam + k ln lam - ln k!.
+static __host__ __device__ __noinline__ bool ptrs_accept64(double lam, long long k, double V, double us, const PtrsConsts &c)
+{
+    const double loglam = dlog(lam);
+    const double inv_alpha = 1.1239 + 1.1328 / (c.b - 3.4);
+    const double kd = u53_to_double((unsigned long long)k);
+    const double lhs = dlog(V * inv_alpha / (c.a / (us * us) + c.b));
+    const double rhs = -lam + kd * loglam - dlnfact(k);
+    return lhs <= rhs;
+}
+static __host__ __device__ __noinline__ long long ptrs_floor64(double lam, double U, double us, const PtrsConsts &c)
+{
+    return floor_to_ll((c.two_a / us + c.b) * U + lam + 0.43);
+}
+
 TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
 {
     // FP64 constants, formed on first need
     bool set64 = false;
-    double b = 0.0, a = 0.0, two_a = 0.0, vr = 0.0;
-    // ln lam and 1/alpha serve only the FP64 acceptance test after the
-    // squeeze, so they are formed on first use (same values)
-    double loglam = 0.0, inv_alpha = 0.0;
-    bool slow_ready = false;
+    PtrsConsts c{0.0, 0.0, 0.0, 0.0};
     // FP32 images for the certified decisions
     const bool f32 = nn_gt(0x1p16, lam);
     float lf = 0.0f, bf = 0.0f, af = 0.0f, vrf = 0.0f, Lhi = 0.0f, Llo = 0.0f;
@@ -688,7 +723,7 @@ TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t atte
                     const float fl = floorf(x);
                     const float fr = x - fl;   // exact
                     if (fr > E && fr < 1.0f - E) {
-                        k = (long long)fl;
+                        k = (long long)(int)fl;   // |fl| < 2^22
                         k_known = true;
                     }
                 }
@@ -697,16 +732,12 @@ TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t atte
         const bool need_k = (acc != 0) || !squeeze_rej;
         if (acc < 0 || (need_k && !k_known)) {
             if (!set64) {
-                const double slam = sqrt(lam);
-                b = 0.931 + 2.53 * slam;
-                a = -0.059 + 0.02483 * b;                                          // > 0 for lam >= 10
-                two_a = bits::ll2d(bits::d2ll(a) + (1ll << 52));                   // 2a, exactly
-                vr = 0.9277 - 3.6224 / (b - 2.0);                                  // > 0 for lam >= 10
+                c = ptrs_consts64(lam);
                 set64 = true;
             }
-            if (acc < 0) acc = (us_ok && nn_ge(vr, V)) ? 1 : 0;
+            if (acc < 0) acc = (us_ok && nn_ge(c.vr, V)) ? 1 : 0;
             if (!k_known && ((acc != 0) || !squeeze_rej)) {
-                k = floor_to_ll((two_a / us + b) * U + lam + 0.43);
+                k = ptrs_floor64(lam, U, us, c);
                 k_known = true;
             }
         }
@@ -714,26 +745,14 @@ TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t atte
         if (squeeze_rej || k < 0) continue;
         if (k > kCountLimit) return kCountLimit + 1;
         const int sure = f32 ? ptrs_accept_certain_f(lf, k, f64_to_f32(V), f64_to_f32(us), af, bf, 2e-5f)
-                             : (set64 ? ptrs_accept_certain(lam, k, V, us, a, b) : 0);
+                             : (set64 ? ptrs_accept_certain(lam, k, V, us, c.a, c.b) : 0);
         if (sure > 0) return k;
         if (sure < 0) continue;
         if (!set64) {
-            const double slam = sqrt(lam);
-            b = 0.931 + 2.53 * slam;
-            a = -0.059 + 0.02483 * b;
-            two_a = bits::ll2d(bits::d2ll(a) + (1ll << 52));
-            vr = 0.9277 - 3.6224 / (b - 2.0);
+            c = ptrs_consts64(lam);
             set64 = true;
         }
-        if (!slow_ready) {
-            loglam = dlog(lam);
-            inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
-            slow_ready = true;
-        }
-        const double kd = u53_to_double((unsigned long long)k);
-        const double lhs = dlog(V * inv_alpha / (a / (us * us) + b));
-        const double rhs = -lam + kd * loglam - dlnfact(k);
-        if (lhs <= rhs) return k;
+        if (ptrs_accept64(lam, k, V, us, c)) return k;
     }
     return -1;
 }

@@ -20,9 +20,13 @@ namespace tl {
 //                  2 second order as X+Y only, 3 some reaction takes 2X
 //   dep_ptr [N+1]  reactions whose propensity reads species i (i is a reactant)
 //   dep_ent [ndep] reaction indices
+//   cinfo [M]      the species reaction j consumes (nu < 0), for the
+//                  critical test: sp_a | n_a << 14 | sp_b << 16 | n_b << 30,
+//                  n = |nu| in {1, 2}, 0 for an absent entry (a reaction of
+//                  order <= 2 consumes at most two species)
 struct ModelLayout {
     int32_t N, M, nnz, ndep;
-    int32_t off_rinfo, off_nu_ptr, off_nu_ent, off_tr_ptr, off_tr_ent, off_hor, off_dep_ptr, off_dep_ent;
+    int32_t off_rinfo, off_nu_ptr, off_nu_ent, off_tr_ptr, off_tr_ent, off_hor, off_dep_ptr, off_dep_ent, off_cinfo;
     int32_t words;
     int32_t max_nu_len;
 };
@@ -46,6 +50,13 @@ struct GroupArgs {
     int32_t *samples;
     ssa_sim_stats *stats;
     int64_t first;
+    // optional completion signal (the serving loop): every finished
+    // simulation adds 1 to *done_count; the one that brings it to n_sims
+    // sets *done_flag (host-mapped memory) to 1 after a system-scope fence,
+    // so the host learns that this group's results are complete while the
+    // launch is still running other groups
+    unsigned long long *done_count;
+    volatile int32_t *done_flag;
 };
 
 struct SimArgs {
@@ -105,18 +116,26 @@ __host__ __device__ inline size_t model_smem_bytes(const ModelLayout &L)
 // Lane-per-simulation FP64 reference kernel (kernel_lane_f64.cu): SSA steps
 // one simulation per lane, leaps and step-size selection warp-cooperative.
 size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps);
-cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+// `carveout`: shared-memory carve-out in percent for this launch, -1 = the driver's default.
+cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
 int lane_ref_occupancy(int block_warps, size_t smem);
 // Fast-mode instantiation (kernel_lane_fast.cu), same shared-memory layout.
-cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
 int lane_fast_occupancy(int block_warps, size_t smem);
 // Multi-network persistent instantiations (model read from global memory;
 // workspace sized for the largest network, no model staged in shared memory).
 size_t lane_multi_smem_bytes(int max_N, int max_M, int block_warps);
-cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
 int lane_multi_ref_occupancy(int block_warps, size_t smem);
-cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
 int lane_multi_fast_occupancy(int block_warps, size_t smem);
+
+// ssa_simulate_multi_dev with optional per-group completion signals
+// (abi.cu): group g counts its finished simulations in done_counts[g]
+// (device memory, zeroed by the caller on `stream`) and its last simulation
+// sets done_flags[g] (host-mapped) to 1.  Both may be null.
+int simulate_multi_impl(int32_t n_groups, const ssa_group *groups, const ssa_options *opts, void *stream,
+                        unsigned long long *done_counts, volatile int32_t *done_flags);
 
 // Sweep moments (moments.cu): mean[c] and unbiased var[c] of every cell c =
 // k*N + i from the exact integer sums accumulated by the lane kernels.

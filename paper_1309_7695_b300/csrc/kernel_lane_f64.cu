@@ -44,18 +44,18 @@ struct RefArith {
 
 size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps) { return lane_smem_bytes(L, block_warps); }
 
-cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
 {
-    return launch_lane_impl<RefArith, false>(a, block_warps, grid, smem, s);
+    return launch_lane_impl<RefArith, false>(a, block_warps, grid, smem, carveout, s);
 }
 
 int lane_ref_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<RefArith, false>(block_warps, smem); }
 
 size_t lane_multi_smem_bytes(int max_N, int max_M, int block_warps) { return lane_multi_bytes(max_N, max_M, block_warps); }
 
-cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
 {
-    return launch_lane_impl<RefArith, true>(a, block_warps, grid, smem, s);
+    return launch_lane_impl<RefArith, true>(a, block_warps, grid, smem, carveout, s);
 }
 
 int lane_multi_ref_occupancy(int block_warps, size_t smem)

@@ -70,16 +70,16 @@ struct FastArith {
 
 }  // namespace
 
-cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
 {
-    return launch_lane_impl<FastArith, false>(a, block_warps, grid, smem, s);
+    return launch_lane_impl<FastArith, false>(a, block_warps, grid, smem, carveout, s);
 }
 
 int lane_fast_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<FastArith, false>(block_warps, smem); }
 
-cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
 {
-    return launch_lane_impl<FastArith, true>(a, block_warps, grid, smem, s);
+    return launch_lane_impl<FastArith, true>(a, block_warps, grid, smem, carveout, s);
 }
 
 int lane_multi_fast_occupancy(int block_warps, size_t smem)

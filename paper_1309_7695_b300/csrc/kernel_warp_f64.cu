@@ -380,7 +380,7 @@ size_t warp_f64_smem_bytes(const ModelLayout &L, int block_warps)
 
 cudaError_t launch_warp_ref(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = f64::ensure_log_table();
+    cudaError_t e = f64::ensure_log_table(s);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(warp_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

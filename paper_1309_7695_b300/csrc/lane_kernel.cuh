@@ -69,7 +69,8 @@ __host__ __device__ inline size_t r16(size_t v) { return (v + 15) & ~size_t(15);
 __host__ __device__ inline size_t lane_warp_bytes(int N, int M)
 {
     return r16(4 * (size_t)kStride * N) + r16(8 * (size_t)kStride * kNodes) + r16(8 * (size_t)M) +
-           r16(8 * (size_t)M) + r16(8 * (size_t)N) + r16((size_t)M) + r16((size_t)N) + r16(4 * (size_t)M);
+           r16(8 * (size_t)M) + r16(8 * (size_t)N) + r16((size_t)M) + r16((size_t)N) + r16(4 * (size_t)M) +
+           r16(8 * (size_t)M) + r16(4 * (size_t)M) + r16(8 * (size_t)N);
 }
 
 struct LaneSmem {
@@ -81,6 +82,9 @@ struct LaneSmem {
     unsigned char *crit;
     unsigned char *irs;
     unsigned short *jl;   // [2M] reactions queued for inversion ([0, M)) and PTRS ([M, 2M))
+    double *c;            // [M] rate constants of the simulation the warp last worked on together
+    float *af;            // [M] FP32 image of a_j for noncritical a_j > 0, else 0 (NaN: out of FP32 range)
+    float2 *lo;           // [N] certified lower bounds of the species' two tau' terms
 };
 
 __device__ __forceinline__ LaneSmem carve_lane(unsigned char *p, int N, int M)
@@ -101,6 +105,12 @@ __device__ __forceinline__ LaneSmem carve_lane(unsigned char *p, int N, int M)
     w.irs = p;
     p += r16((size_t)N);
     w.jl = reinterpret_cast<unsigned short *>(p);
+    p += r16(4 * (size_t)M);
+    w.c = reinterpret_cast<double *>(p);
+    p += r16(8 * (size_t)M);
+    w.af = reinterpret_cast<float *>(p);
+    p += r16(4 * (size_t)M);
+    w.lo = reinterpret_cast<float2 *>(p);
     return w;
 }
 
@@ -108,7 +118,7 @@ constexpr double kDblMax = 1.7976931348623157e308;
 
 // Everything one simulation group needs: network arrays and run arguments.
 struct GroupView {
-    const int *rinfo, *nu_ptr, *nu_ent, *tr_ptr, *tr_ent, *hor, *dep_ptr, *dep_ent;
+    const int *rinfo, *nu_ptr, *nu_ent, *tr_ptr, *tr_ent, *hor, *dep_ptr, *dep_ent, *cinfo;
     int N, M, S;
     double t_end;
     const double *params;
@@ -119,6 +129,8 @@ struct GroupView {
     unsigned long long *moments;
     long long sim_offset, n_sims, first;
     uint64_t seed;
+    unsigned long long *done_count;
+    volatile int32_t *done_flag;
 };
 
 // One recorded count of simulation `row`, sample k, species i: stored in the
@@ -146,6 +158,7 @@ __device__ __forceinline__ void view_model(GroupView &G, const int *blob, const 
     G.hor = blob + L.off_hor;
     G.dep_ptr = blob + L.off_dep_ptr;
     G.dep_ent = blob + L.off_dep_ent;
+    G.cinfo = blob + L.off_cinfo;
     G.N = L.N;
     G.M = L.M;
 }
@@ -167,6 +180,8 @@ __device__ __forceinline__ GroupView view_single(const SimArgs &A, const int *sm
     G.n_sims = A.n_sims;
     G.first = 0;
     G.seed = A.seed;
+    G.done_count = nullptr;
+    G.done_flag = nullptr;
     return G;
 }
 
@@ -188,6 +203,8 @@ __device__ __forceinline__ GroupView view_group(const GroupArgs *groups, int g)
     G.n_sims = R.n_sims;
     G.first = R.first;
     G.seed = R.seed;
+    G.done_count = R.done_count;
+    G.done_flag = R.done_flag;
     return G;
 }
 
@@ -231,9 +248,39 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
     int first = 0;
     long long leaps = 0, rejected = 0, ssa_steps = 0, firings = 0;
     double tnext = kInf;   // T[ks], or +inf once every sample is recorded
+    // warp-uniform: the (group, row) whose rate constants are in w.c
+    long long c_row = -1;
+    int c_grp = -1;
+    // FP32 images of eps and ssa_factor for the certified bounds (a factor
+    // above 1e30 leaves every SSA-fallback test to FP64)
+    const float epsf = f64::f64_to_f32(A.eps);
+    const float ssaf = f64::f64_to_f32(A.ssa_factor);
+    const bool ssaf_ok = f64::nn_ge(1e30, A.ssa_factor);
 
     auto own_prop = [&](const GroupView &G, int j) -> double {
         return Arith::prop(G.rinfo[j], __ldg(G.params + (size_t)row * G.M + j), X, kStride, lane);
+    };
+    // Slot sum of this lane's simulation, S_l = sum over j = l, l+32, ... of
+    // a_j in increasing j (the canonical order).  Up to four reactions per
+    // slot (M <= 128) their rate constants are loaded together before the
+    // first is used, so the global-memory latency is paid once per slot.
+    auto own_slot_sum = [&](const GroupView &G, int l) -> double {
+        const double *c = G.params + (size_t)row * G.M;
+        const int M = G.M;
+        if (M <= 128) {
+            const double c0 = __ldg(c + l);
+            const double c1 = (l + 32 < M) ? __ldg(c + l + 32) : 0.0;
+            const double c2 = (l + 64 < M) ? __ldg(c + l + 64) : 0.0;
+            const double c3 = (l + 96 < M) ? __ldg(c + l + 96) : 0.0;
+            double s = f64::first_term(Arith::prop(G.rinfo[l], c0, X, kStride, lane));
+            if (l + 32 < M) s = s + Arith::prop(G.rinfo[l + 32], c1, X, kStride, lane);
+            if (l + 64 < M) s = s + Arith::prop(G.rinfo[l + 64], c2, X, kStride, lane);
+            if (l + 96 < M) s = s + Arith::prop(G.rinfo[l + 96], c3, X, kStride, lane);
+            return s;
+        }
+        double s = f64::first_term(own_prop(G, l));
+        for (int j = l + 32; j < M; j += 32) s = s + own_prop(G, j);
+        return s;
     };
     auto lane_record = [&](const GroupView &G, int k) {
         for (int i = 0; i < G.N; ++i) record_count(G, row, k, i, X[i * kStride + lane]);
@@ -298,8 +345,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                 const int L = __ffs(todo) - 1;
                 todo &= todo - 1;
                 const GroupView GL = gview(__shfl_sync(kFull, grp, L));
-                const int *rinfo = GL.rinfo, *nu_ptr = GL.nu_ptr, *nu_ent = GL.nu_ent, *tr_ptr = GL.tr_ptr,
-                          *tr_ent = GL.tr_ent, *hor = GL.hor;
+                const int *rinfo = GL.rinfo, *tr_ptr = GL.tr_ptr, *tr_ent = GL.tr_ent, *hor = GL.hor;
                 const int N = GL.N, M = GL.M, S = GL.S;
                 const double *T = GL.T;
                 const double t_end = GL.t_end;
@@ -314,7 +360,15 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                 long long fiL = fi0;
                 int stL = SSA_STATUS_OK;
                 int nphase = P_TOP, nleft = 0, nfirst = 0;
-                const double *cL = GL.params + (size_t)rL * M;
+                // rate constants of simulation L, cached per warp in shared memory: a
+                // long simulation's consecutive leaps read them from there
+                const int gL = kMulti ? __shfl_sync(kFull, grp, L) : 0;
+                if (rL != c_row || gL != c_grp) {
+                    const double *cL = GL.params + (size_t)rL * M;
+                    for (int j = lane; j < M; j += 32) w.c[j] = __ldg(cL + j);
+                    c_row = rL;
+                    c_grp = gL;
+                }
 
                 double tnL = __shfl_sync(kFull, tnext, L);
                 while (ksL < S && tnL <= tL) {
@@ -330,12 +384,12 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                 } else {
                     double s = 0.0;
                     if (lane < M) {   // first term of the slot sum (no add to +0)
-                        const double a = Arith::prop(rinfo[lane], cL[lane], X, kStride, L);
+                        const double a = Arith::prop(rinfo[lane], w.c[lane], X, kStride, L);
                         w.a[lane] = a;
                         s = f64::first_term(a);
                     }
                     for (int j = lane + 32; j < M; j += 32) {
-                        const double a = Arith::prop(rinfo[j], cL[j], X, kStride, L);
+                        const double a = Arith::prop(rinfo[j], w.c[j], X, kStride, L);
                         w.a[j] = a;
                         s = s + a;
                     }
@@ -352,21 +406,32 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         stL = SSA_STATUS_INVALID;
                         nphase = P_DONE;
                     } else {
-                        // critical set (CGP 2005)
+                        // critical set (CGP 2005): L_j = min over the species j consumes of
+                        // floor(x_i / |nu_ij|), read from the packed consumed-species word
+                        const int *cinfo = GL.cinfo;
+                        bool any_crit = false;
                         for (int j = lane; j < M; j += 32) {
-                            long long Lj = LLONG_MAX;
-                            for (int e = nu_ptr[j]; e < nu_ptr[j + 1]; ++e) {
-                                const int ent = nu_ent[e];
-                                const int nv = (signed char)(ent & 0xff);
-                                if (nv < 0) {
-                                    // a consumed species has |nu| <= 2 (reactant coefficients <= 2)
-                                    const int xq = X[(ent >> 8) * kStride + L];
-                                    const long long q = (nv == -1) ? xq : (xq >> 1);
-                                    Lj = q < Lj ? q : Lj;
-                                }
+                            const unsigned ci = (unsigned)cinfo[j];
+                            const unsigned na = (ci >> 14) & 3u, nb = ci >> 30;
+                            const int xa = X[(ci & 0x3fffu) * kStride + L];
+                            const int xb = X[((ci >> 16) & 0x3fffu) * kStride + L];
+                            int Lj = INT_MAX;
+                            if (na) Lj = (na == 1) ? xa : (xa >> 1);
+                            if (nb) Lj = min(Lj, (nb == 1) ? xb : (xb >> 1));
+                            const double a = w.a[j];
+                            const bool cr = f64::nn_pos(a) && (Lj < A.n_c);
+                            w.crit[j] = cr;
+                            any_crit |= cr;
+                            // FP32 image of a noncritical positive propensity for the bounds
+                            // below; NaN marks a value outside the range they are proved for
+                            float af = 0.0f;
+                            if (!cr && f64::nn_pos(a)) {
+                                const int ea = (int)(f64::dbits(a) >> 52);
+                                af = (ea >= 1023 - 100 && ea <= 1023 + 100) ? f64::f64_to_f32(a) : __int_as_float(0x7fc00000);
                             }
-                            w.crit[j] = f64::nn_pos(w.a[j]) && (Lj < (long long)A.n_c);
+                            w.af[j] = af;
                         }
+                        any_crit = __any_sync(kFull, any_crit);
                         for (int i = lane; i < N; i += 32) w.irs[i] = 0;
                         __syncwarp();
                         for (int j = lane; j < M; j += 32) {
@@ -377,79 +442,86 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             if (kind == 2) w.irs[(info >> 17) & 0x7fff] = 1;
                         }
                         __syncwarp();
-                        // Screen: the canonical decision "tau' < ssa_factor / a0" (SSA
-                        // block) is often certain from FP32.  An FP32 evaluation bounds
-                        // every tau' term from above: mu and sigma^2 summed in FP32 from
-                        // the FP32 images of a_j are within (n + 4) 2^-20 of the sum of
-                        // |nu a| of the FP64 sums, and bound = max(eps x / g, 1) within
-                        // 2^-20 relative; the upper bounds carry a further 1e-4 and the
-                        // threshold's lower bound 1e-4.  A term whose mu is not certainly
-                        // nonzero is left out (a minimum over fewer terms is still an
-                        // upper bound).  When the bound on tau' lies below the bound on
-                        // the threshold, the canonical decision is the SSA block, and the
-                        // FP64 sums, divisions and the a0c tree are skipped.
-                        bool certain_ssa = false;
-                        {
-                            unsigned qmin = 0x7F800000u;   // +inf as float bits
-                            for (int i = lane; i < N; i += 32) {
-                                if (!w.irs[i]) continue;
+                        // Certified FP32 bounds on every tau' term (CGP 2006).  mu and sigma^2
+                        // summed in FP32 from the FP32 images of the a_j are within
+                        // (n + 4) 2^-20 of the sum of |nu a| of the exact sums (n terms), and
+                        // bound = max(eps x / g, 1) within 2^-20 relative; each bound below
+                        // carries a further 1e-4.  A term whose mu is not certainly nonzero
+                        // gets the upper bound +inf.  From these:
+                        //  - the SSA-fallback decision "tau' < ssa_factor / a0" is certain when
+                        //    the smallest upper bound lies below a lower bound of the threshold;
+                        //  - otherwise tau' = the smallest exact term, and only terms whose lower
+                        //    bound does not exceed the smallest upper bound can be that term, so
+                        //    only those are computed in FP64 (in the canonical operations).
+                        const float kNoTerm = __int_as_float(0x7fc00000);   // NaN: never a candidate
+                        unsigned hmin = 0x7F800000u;                          // +inf as float bits
+                        for (int i = lane; i < N; i += 32) {
+                            float2 lo = make_float2(kNoTerm, kNoTerm);
+                            if (w.irs[i]) {
                                 float muf = 0.0f, s2f = 0.0f, absf = 0.0f;
                                 int n = 0;
                                 for (int e = tr_ptr[i]; e < tr_ptr[i + 1]; ++e) {
                                     const int ent = tr_ent[e];
-                                    const int j = ent >> 8;
-                                    if (w.crit[j]) continue;
-                                    const double a = w.a[j];
-                                    if (!f64::nn_pos(a)) continue;
-                                    const float af = f64::f64_to_f32(a);
+                                    const float af = w.af[ent >> 8];
+                                    if (af == 0.0f) continue;
                                     const float nvf = (float)(signed char)(ent & 0xff);
                                     muf = muf + nvf * af;
                                     s2f = s2f + (nvf * nvf) * af;
                                     absf = absf + fabsf(nvf) * af;
                                     ++n;
                                 }
-                                if (n == 0) continue;
-                                const int xi = X[i * kStride + L];
-                                const float xf = (float)xi;
-                                const int h = hor[i];
-                                float bf = (float)A.eps * xf;
-                                if (h == 2 || (h != 1 && xi < 2)) bf = bf * 0.5f;
-                                else if (h != 1) bf = bf / (2.0f + 1.0f / (xf - 1.0f));
-                                bf = fmaxf(bf, 1.0f) * 1.000001f;   // >= canonical bound
-                                const float err = (float)(n + 4) * 0x1p-20f * absf;
-                                const float amu = fabsf(muf);
-                                if (amu > 2.0f * err) {
-                                    const float q1 = (bf * 1.0001f) / (amu - err);
-                                    qmin = min(qmin, __float_as_uint(q1));
+                                if (n > 0) {
+                                    const int xi = X[i * kStride + L];
+                                    const float xf = (float)xi;
+                                    const int h = hor[i];
+                                    float bf = epsf * xf;
+                                    if (h == 2 || (h != 1 && xi < 2)) bf = bf * 0.5f;
+                                    else if (h != 1) bf = bf / (2.0f + 1.0f / (xf - 1.0f));
+                                    bf = fmaxf(bf, 1.0f);
+                                    const float b_hi = bf * (1.0f + 0x1p-20f), b_lo = bf * (1.0f - 0x1p-20f);
+                                    const float rel = (float)(n + 4) * 0x1p-20f;
+                                    const float err = rel * absf;
+                                    const float amu = fabsf(muf);
+                                    // term 1: bound / |mu|
+                                    float lo1 = (b_lo / (amu + err)) * (1.0f - 1e-4f);
+                                    float hi1 = (amu > err) ? (b_hi / (amu - err)) * (1.0f + 1e-4f) : __int_as_float(0x7F800000);
+                                    // term 2: bound^2 / sigma^2 (all terms positive: no cancellation)
+                                    float lo2 = ((b_lo * b_lo) / (s2f * (1.0f + rel))) * (1.0f - 2e-4f);
+                                    float hi2 = ((b_hi * b_hi) / (s2f * (1.0f - rel))) * (1.0f + 2e-4f);
+                                    // outside the proved range (NaN inputs, overflow, underflow):
+                                    // always a candidate, never an upper bound
+                                    if (!(lo1 >= 0x1p-120f && hi1 <= 0x1p120f)) {
+                                        lo1 = 0.0f;
+                                        hi1 = __int_as_float(0x7F800000);
+                                    }
+                                    if (!(lo2 >= 0x1p-120f && hi2 <= 0x1p120f)) {
+                                        lo2 = 0.0f;
+                                        hi2 = __int_as_float(0x7F800000);
+                                    }
+                                    lo = make_float2(lo1, lo2);
+                                    hmin = min(hmin, min(__float_as_uint(hi1), __float_as_uint(hi2)));
                                 }
-                                const float q2 = ((bf * bf) * 1.0002f) / (s2f * (1.0f - (float)(n + 4) * 0x1p-20f));
-                                if (q2 > 0.0f) qmin = min(qmin, __float_as_uint(q2));
                             }
-                            qmin = __reduce_min_sync(kFull, qmin);
-                            const float thr_lo = ((float)A.ssa_factor / f64::f64_to_f32(a0)) * 0.9999f;
-                            certain_ssa = __uint_as_float(qmin) < thr_lo;
+                            w.lo[i] = lo;
                         }
-                        if (certain_ssa) {
+                        hmin = __reduce_min_sync(kFull, hmin);
+                        const float tau1_hi = __uint_as_float(hmin);
+                        // the threshold ssa_factor / a0 in FP32, and whether its image is trusted
+                        const int e0 = (int)(f64::dbits(a0) >> 52);
+                        const bool thr_ok = ssaf_ok && (e0 >= 1023 - 100 && e0 <= 1023 + 100);
+                        const float thr_f = ssaf / f64::f64_to_f32(a0);
+                        const float thr_lo = thr_f * (1.0f - 1e-5f), thr_hi = thr_f * (1.0f + 1e-5f);
+                        if (thr_ok && tau1_hi < thr_lo) {
                             nphase = P_SSA;
                             nleft = A.ssa_block;
                             nfirst = 1;
                         } else {
-                        double sc = 0.0;
-                        bool sc_started = false;   // the first critical term is taken, not added to +0
-                        for (int j = lane; j < M; j += 32) {
-                            if (!w.crit[j]) continue;
-                            const double a = w.a[j];   // > 0
-                            if (sc_started) sc = sc + a;
-                            else sc = a;
-                            sc_started = true;
-                        }
-                        double Lc[6];
-                        const double a0c = slot_tree(sc, Lc);
-                        const double ssa_thr = A.ssa_factor / a0;   // the SSA-fallback threshold
-                        // tau' (CGP 2006) over the reactant species of noncritical reactions
+                        // tau' exactly: the canonical FP64 terms of the candidate species
                         unsigned long long tmin = 0x7FF0000000000000ull;
                         for (int i = lane; i < N; i += 32) {
-                            if (!w.irs[i]) continue;
+                            const float2 lo = w.lo[i];
+                            const bool need1 = lo.x <= tau1_hi, need2 = lo.y <= tau1_hi;
+                            if (!(need1 || need2)) continue;
                             double mu = 0.0, sig2 = 0.0;
                             for (int e = tr_ptr[i]; e < tr_ptr[i + 1]; ++e) {
                                 const int ent = tr_ent[e];
@@ -487,22 +559,56 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             else if (h == 2 || xi < 2) bound = ex * 0.5;
                             else bound = ex / (2.0 + 1.0 / (xd - 1.0));
                             if (f64::dbits(bound) < f64::dbits(1.0)) bound = 1.0;
-                            if ((f64::dbits(mu) << 1) != 0) {   // mu != 0
+                            if (need1 && (f64::dbits(mu) << 1) != 0) {   // mu != 0
                                 const unsigned long long b1 =
                                     (unsigned long long)__double_as_longlong(bound / fabs(mu));
                                 tmin = b1 < tmin ? b1 : tmin;
                             }
-                            if (f64::nn_pos(sig2)) {   // sig2 >= 0; != 0
+                            if (need2 && f64::nn_pos(sig2)) {   // sig2 >= 0; != 0
                                 const unsigned long long b2 =
                                     (unsigned long long)__double_as_longlong((bound * bound) / sig2);
                                 tmin = b2 < tmin ? b2 : tmin;
                             }
                         }
                         double tau1 = __longlong_as_double((long long)warp_min_u64(tmin));
+                        // a0c (the canonical sum of the critical propensities), needed only
+                        // when a critical reaction exists; otherwise it is +0
+                        double Lc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                        double a0c = 0.0;
+                        if (any_crit) {
+                            double sc = 0.0;
+                            bool sc_started = false;   // the first critical term is taken, not added to +0
+                            for (int j = lane; j < M; j += 32) {
+                                if (!w.crit[j]) continue;
+                                const double a = w.a[j];   // > 0
+                                if (sc_started) sc = sc + a;
+                                else sc = a;
+                                sc_started = true;
+                            }
+                            a0c = slot_tree(sc, Lc);
+                        }
+                        // the SSA-fallback test tau' < ssa_factor / a0: decided on the FP32
+                        // images when they are clear of the threshold's margin, else by the
+                        // FP64 division (formed once)
+                        double ssa_thr = 0.0;
+                        bool thr_ready = false;
+                        auto below_threshold = [&](double tau) -> bool {
+                            const int et = (int)(f64::dbits(tau) >> 52);   // tau > 0
+                            if (thr_ok && et >= 1023 - 120 && et <= 1023 + 120) {
+                                const float tf = f64::f64_to_f32(tau);
+                                if (tf < thr_lo) return true;
+                                if (tf > thr_hi) return false;
+                            }
+                            if (!thr_ready) {
+                                ssa_thr = A.ssa_factor / a0;
+                                thr_ready = true;
+                            }
+                            return tau < ssa_thr;
+                        };
 
                         int halvings = 0;
                         for (;;) {
-                            if (tau1 < ssa_thr) {
+                            if (below_threshold(tau1)) {
                                 nphase = P_SSA;
                                 nleft = A.ssa_block;
                                 nfirst = 1;
@@ -756,8 +862,13 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         }
                         double cum = 0.0;
                         int jf = -1, last = -1;
+                        // walk the slot; the next member's rate constant is loaded one step ahead
+                        const double *cp = G.params + (size_t)row * M;
+                        double cnext = __ldg(cp + cls);
                         for (int j = cls; j < M; j += 32) {
-                            const double v = own_prop(G, j);
+                            const double cj = cnext;
+                            if (j + 32 < M) cnext = __ldg(cp + j + 32);
+                            const double v = Arith::prop(G.rinfo[j], cj, X, kStride, lane);
                             if (j == cls) cum = f64::first_term(v);
                             else cum = cum + v;
                             if (f64::nn_pos(v)) last = j;
@@ -793,9 +904,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 while (m) {
                                     const int l = __ffs(m) - 1;
                                     m &= m - 1;
-                                    double s = f64::first_term(own_prop(G, l));   // l < M: a dirty slot holds a reaction
-                                    for (int j = l + 32; j < M; j += 32) s = s + own_prop(G, j);
-                                    V[l * kStride + lane] = s;
+                                    V[l * kStride + lane] = own_slot_sum(G, l);   // l < M: a dirty slot holds a reaction
                                 }
 #pragma unroll
                                 for (int k = 1; k <= 5; ++k) {
@@ -838,6 +947,16 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                 st.t_final = t;
                 G.stats[row] = st;
             }
+            if (kMulti && G.done_count != nullptr) {
+                // this simulation's samples and counters are written: count it, and the
+                // group's last simulation tells the host that the group is complete
+                __threadfence();
+                const unsigned long long prev = atomicAdd(G.done_count, 1ull);
+                if (prev + 1 == (unsigned long long)G.n_sims) {
+                    __threadfence_system();
+                    *G.done_flag = 1;
+                }
+            }
             phase = P_NEED;
         }
         __syncwarp();
@@ -857,11 +976,13 @@ inline size_t lane_multi_bytes(int max_N, int max_M, int block_warps)
 }
 
 template <class Arith, bool kMulti>
-cudaError_t launch_lane_impl(const SimArgs &a, int block_warps, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_lane_impl(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
 {
-    cudaError_t e = f64::ensure_log_table();
+    cudaError_t e = f64::ensure_log_table(s);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     if (e != cudaSuccess) return e;
     lane::lane_kernel<Arith, kMulti><<<grid, block_warps * 32, smem, s>>>(a);
     return cudaGetLastError();
@@ -871,8 +992,11 @@ template <class Arith, bool kMulti>
 int lane_occupancy_impl(int block_warps, size_t smem)
 {
     int nb = 0;
+    // the carve-out a previous launch may have set would cap the answer: query at the default
     if (cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributePreferredSharedMemoryCarveout, -1) !=
+            cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lane::lane_kernel<Arith, kMulti>, block_warps * 32, smem) !=
         cudaSuccess)

@@ -4,13 +4,18 @@
 // ssa_server_submit.  A dispatcher thread admits queued requests, in arrival
 // order, whenever a stream slot is free and the request's HBM footprint fits
 // the remaining budget; all requests admitted together form one
-// multi-network persistent launch (ssa_simulate_multi_dev) on that slot's
-// stream, so batches on different slots overlap on the device.  Results stay
-// resident in device memory until ssa_server_fetch copies them out and frees
-// them, which returns their bytes to the budget.  Each simulation's random
-// stream is keyed by (request seed, replicate index) and every launch uses
-// the same kernel, so a request's result does not depend on what it was
-// batched or overlapped with.
+// multi-network persistent launch on that slot's stream, so batches on
+// different slots overlap on the device.  Each request of a launch is one
+// group of the launch and completes on its own: the kernel counts the
+// group's finished simulations and its last one raises the request's flag
+// in host-mapped memory, which the dispatcher polls, so a short request does
+// not wait for the long ones it was batched with.  Results stay resident in
+// device memory until ssa_server_fetch copies them out (on a stream of its
+// own, not behind later launches on the slot) and frees them, which returns
+// their bytes to the budget.  Each simulation's random stream is keyed by
+// (request seed, replicate index) and every launch uses the same kernel, so
+// a request's result does not depend on what it was batched or overlapped
+// with.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -54,6 +59,7 @@ struct Request {
     double t_submit = 0, t_admit = -1, t_done = -1;
     int32_t batch_size = 0;
     int slot = -1;
+    int flag = -1;   // index of its completion flag / counter while its launch runs
     // device buffers (valid from admission until fetch)
     double *d_params = nullptr, *d_T = nullptr;
     int32_t *d_x0 = nullptr, *d_samples = nullptr;
@@ -85,6 +91,11 @@ struct ssa_server {
     bool shutdown = false;
     std::thread worker;
     int64_t launches = 0;
+    // completion signals, max_batch per slot: flags in host-mapped memory
+    // (h_flags, seen by the device as d_flags), counters in device memory
+    int32_t *h_flags = nullptr;
+    int32_t *d_flags = nullptr;
+    unsigned long long *d_counts = nullptr;
 
     void run();
 };
@@ -106,8 +117,18 @@ void ssa_server::run()
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lock(mu);
     for (;;) {
-        cv.wait_for(lock, std::chrono::milliseconds(5));
-        // completions
+        cv.wait_for(lock, inflight.empty() ? std::chrono::milliseconds(5) : std::chrono::milliseconds(1));
+        bool woke = false;
+        // per-request completions: flags raised by the kernel for finished groups
+        for (auto &bp : inflight)
+            for (auto &r : bp->reqs)
+                if (r->t_done < 0 && r->flag >= 0 && reinterpret_cast<volatile int32_t *>(h_flags)[r->flag] != 0) {
+                    r->t_done = now_s(t0);
+                    r->state = SSA_JOB_DONE;
+                    woke = true;
+                }
+        // whole launches: free the slot; requests without a raised flag (no
+        // simulations, or a failed launch) complete here
         for (size_t k = 0; k < inflight.size();) {
             Batch &b = *inflight[k];
             if (!b.done) {
@@ -117,18 +138,21 @@ void ssa_server::run()
             cudaError_t e = cudaStreamQuery(streams[(size_t)b.slot]);
             const double t = now_s(t0);
             for (auto &r : b.reqs) {
-                r->t_done = t;
                 if (e != cudaSuccess && e != cudaErrorNotReady) {
                     r->state = SSA_JOB_FAILED;
                     r->error = cudaGetErrorString(e);
-                } else {
+                    if (r->t_done < 0) r->t_done = t;
+                } else if (r->t_done < 0) {
                     r->state = SSA_JOB_DONE;
+                    r->t_done = t;
                 }
+                r->flag = -1;
             }
             slot_busy[(size_t)b.slot] = false;
             inflight.erase(inflight.begin() + (long)k);
-            cv.notify_all();
+            woke = true;
         }
+        if (woke) cv.notify_all();
         if (shutdown && pending.empty() && inflight.empty()) break;
         // admission: FIFO, as many queued requests as fit one free slot and the budget
         int slot = -1;
@@ -154,15 +178,19 @@ void ssa_server::run()
         batch->slot = slot;
         batch->reqs = take;
         cudaStream_t st = streams[(size_t)slot];
+        const int fbase = slot * cfg.max_batch;
         lock.unlock();
         // allocate, copy in, launch (outside the lock: copies from pageable memory block this thread)
         std::vector<ssa_group> groups;
         cudaError_t e = cudaSuccess;
         const double t_adm = now_s(t0);
-        for (auto &r : take) {
+        for (size_t k = 0; k < take.size(); ++k) {
+            auto &r = take[k];
             r->t_admit = t_adm;
             r->slot = slot;
             r->batch_size = (int32_t)take.size();
+            // the slot's previous launch has finished, so its flags are free to clear
+            reinterpret_cast<volatile int32_t *>(h_flags)[fbase + (int)k] = 0;
             const size_t S = r->T.size();
             if (e == cudaSuccess) e = cudaMallocAsync((void **)&r->d_params, sizeof(double) * r->params.size() + 8, st);
             if (e == cudaSuccess) e = cudaMallocAsync((void **)&r->d_x0, sizeof(int32_t) * r->x0.size() + 8, st);
@@ -190,10 +218,13 @@ void ssa_server::run()
             g.stats = r->d_stats;
             groups.push_back(g);
         }
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(d_counts + fbase, 0, sizeof(unsigned long long) * take.size(), st);
         int rc = SSA_ECUDA;
         std::string msg = e == cudaSuccess ? "" : cudaGetErrorString(e);
         if (e == cudaSuccess) {
-            rc = ssa_simulate_multi_dev((int32_t)groups.size(), groups.data(), &cfg.opts, st);
+            rc = tl::simulate_multi_impl((int32_t)groups.size(), groups.data(), &cfg.opts, st, d_counts + fbase,
+                                         d_flags + fbase);
             if (rc != SSA_OK) msg = ssa_last_error();
         }
         if (rc == SSA_OK) {
@@ -206,6 +237,7 @@ void ssa_server::run()
         lock.lock();
         ++launches;
         if (rc == SSA_OK) {
+            for (size_t k = 0; k < take.size(); ++k) take[k]->flag = fbase + (int)k;
             inflight.push_back(batch);
         } else {
             for (auto &r : take) {
@@ -256,6 +288,16 @@ int ssa_server_create(const ssa_server_config *cfg, ssa_server_t *out)
     srv->slot_busy.assign((size_t)c.n_streams, false);
     for (auto &s : srv->streams)
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return sfail(SSA_ECUDA, "stream create failed");
+    const size_t n_sig = (size_t)c.n_streams * (size_t)c.max_batch;
+    if (cudaHostAlloc((void **)&srv->h_flags, sizeof(int32_t) * n_sig, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&srv->d_flags, srv->h_flags, 0) != cudaSuccess ||
+        cudaMalloc((void **)&srv->d_counts, sizeof(unsigned long long) * n_sig) != cudaSuccess) {
+        if (srv->h_flags) cudaFreeHost(srv->h_flags);
+        if (srv->d_counts) cudaFree(srv->d_counts);
+        for (auto &s : srv->streams) cudaStreamDestroy(s);
+        return sfail(SSA_ECUDA, "completion-signal allocation failed");
+    }
+    std::memset(srv->h_flags, 0, sizeof(int32_t) * n_sig);
     srv->t0 = std::chrono::steady_clock::now();
     srv->worker = std::thread([p = srv.get()] { p->run(); });
     *out = srv.release();
@@ -354,10 +396,13 @@ int ssa_server_fetch(ssa_server_t srv, int64_t ticket, int32_t *samples, ssa_sim
     int rc = SSA_OK;
     std::string msg;
     cudaSetDevice(srv->device);
-    cudaStream_t st = srv->streams[(size_t)r->slot];
-    if (r->state == SSA_JOB_DONE) {
+    // a stream of this fetch's own: the copies and frees wait for nothing
+    // else that runs on the device (the request's results are complete; its
+    // launch may still be running other requests)
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess && r->state == SSA_JOB_DONE) {
         const size_t bs = sizeof(int32_t) * (size_t)r->n_sims * r->T.size() * r->N;
-        cudaError_t e = cudaSuccess;
         if (samples && bs) e = cudaMemcpyAsync(samples, r->d_samples, bs, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && stats && r->n_sims)
             e = cudaMemcpyAsync(stats, r->d_stats, sizeof(ssa_sim_stats) * (size_t)r->n_sims, cudaMemcpyDeviceToHost, st);
@@ -366,12 +411,16 @@ int ssa_server_fetch(ssa_server_t srv, int64_t ticket, int32_t *samples, ssa_sim
             rc = SSA_ECUDA;
             msg = cudaGetErrorString(e);
         }
+    } else if (e != cudaSuccess) {
+        rc = SSA_ECUDA;
+        msg = cudaGetErrorString(e);
     } else {
         rc = SSA_ECUDA;
         msg = r->error;
     }
     for (void *p : {(void *)r->d_params, (void *)r->d_x0, (void *)r->d_T, (void *)r->d_samples, (void *)r->d_stats})
-        if (p) cudaFreeAsync(p, st);
+        if (p) cudaFreeAsync(p, st ? st : srv->streams[(size_t)r->slot]);
+    if (st) cudaStreamDestroy(st);   // its frees complete on the device afterwards
     {
         std::lock_guard<std::mutex> lock(srv->mu);
         if (r->t_admit >= 0) srv->used -= r->bytes;
@@ -411,6 +460,8 @@ int ssa_server_destroy(ssa_server_t srv)
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
+    cudaFreeHost(srv->h_flags);
+    cudaFree(srv->d_counts);
     delete srv;
     return SSA_OK;
 }

@@ -82,17 +82,22 @@ __device__ __forceinline__ long long warp_sum_i64(long long v)
 
 // Propensity with the counts stored as one column of a [N][stride] array.
 // Counts are non-negative, so their conversions to double are assembled
-// from bits (same values as the rounding conversion).
+// from bits (same values as the rounding conversion).  Written without
+// branches on the reaction kind, so that lanes of a warp holding reactions
+// of different kinds issue the same two multiplies: a = (c h0) h1 with
+// (h0, h1) = (1, 1), (x, 1), (x, y) or (x(x-1)/2, 1); a product with 1.0 is
+// exact, so the values are those of c, c x, (c x) y and c (x(x-1)/2).
 __device__ __forceinline__ double propensity_col(int info, double c, const int *X, int stride, int col)
 {
     const int kind = info & 3;
     const int s0 = (info >> 2) & 0x7fff;
     const int s1 = (info >> 17) & 0x7fff;
-    if (kind == 0) return c;
-    if (kind == 1) return c * f64::count_to_double(X[s0 * stride + col]);
-    if (kind == 2) return (c * f64::count_to_double(X[s0 * stride + col])) * f64::count_to_double(X[s1 * stride + col]);
-    const long long xi = X[s0 * stride + col];
-    return c * f64::u53_to_double((unsigned long long)((xi * (xi - 1)) / 2));
+    const long long x0 = X[s0 * stride + col];
+    const int x1 = X[s1 * stride + col];
+    const unsigned long long h0 = (kind == 3) ? (unsigned long long)((x0 * (x0 - 1)) / 2) : (unsigned long long)x0;
+    const double d0 = (kind == 0) ? 1.0 : f64::u53_to_double(h0);
+    const double d1 = (kind == 2) ? f64::count_to_double(x1) : 1.0;
+    return (c * d0) * d1;
 }
 
 }  // namespace tl

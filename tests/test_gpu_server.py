@@ -94,3 +94,31 @@ def test_fp64_requests_equal_the_oracle():
         assert np.array_equal(s, rs)
         assert np.array_equal(st["firings"], rst["firings"])
     srv.close()
+
+
+def test_short_request_completes_before_the_long_one_it_is_batched_with():
+    # one stream slot: while a first request runs, a long and a short request
+    # queue up and are then admitted together into one launch; the short one
+    # must complete (and be fetchable) long before the launch ends
+    long_b = inputs.random_batch(32, 64, 2048, seed=3, t_end=100.0, n_samples=11)
+    short_b = inputs.mm_batch(8, seed=4, t_end=1.0, n_samples=3)
+    models = {b.network.name: abi.Model(b.network) for b in (long_b, short_b)}
+    opts = abi.ssa_default_options(precision=abi.SSA_FAST, max_attempts=1 << 18)
+    srv = abi.Server(n_streams=1, max_batch=4, opts=opts)
+
+    def submit(b, seed):
+        return srv.submit(models[b.network.name], b.params, b.x0, b.t_end, b.sample_times, seed)
+
+    first = submit(long_b, 1)
+    t_long, t_short = submit(long_b, 2), submit(short_b, 3)
+    s_short, st_short = srv.fetch(t_short)
+    i_long = srv.poll(t_long)
+    assert i_long.t_done < 0, "the long request should still be running when the short one is fetched"
+    i_long = srv.wait(t_long)
+    srv.fetch(t_long)
+    srv.fetch(first)
+    alone = run_alone(srv, models, [(short_b.network, short_b.params, short_b.x0, short_b.t_end,
+                                     short_b.sample_times, 3)])
+    assert np.array_equal(alone[0][0], s_short) and np.array_equal(alone[0][1], st_short)
+    assert i_long.batch_size == 2
+    srv.close()
