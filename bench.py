@@ -9,11 +9,12 @@ mode (bit-exact with the CPU oracle).  Every simulation runs to t_end or to a
 budget of 2^20 leap attempts + SSA steps.
 
 A step simulates one such batch with its own seed (inputs resident in
-HBM).  By default the K timed steps run as K batches in flight, one launch
-per batch on its own stream (--schedule streams), so the long-running
-simulations of one batch overlap the bulk of the next; --schedule multi
-puts them in one persistent multi-group launch, and --schedule serial times
-one launch per batch, one after another.  Reported: reaction
+HBM).  By default the K timed steps run as one persistent launch over the K
+batches (--schedule multi): lanes take simulations from every batch through
+one work counter, so a lane whose simulation ends early takes the next one
+instead of idling while the long simulations of its batch finish;
+--schedule streams runs one launch per batch on its own stream, and
+--schedule serial one launch per batch, one after another.  Reported: reaction
 firings/s (value) and sim-steps/s (accepted leaps + SSA events), the same
 batches in fast mode, the same metric end to end through the host-buffer
 C ABI with one job per step in flight (e2e), the roofline position of the
@@ -47,22 +48,55 @@ METRIC = "reaction firings/s & sim-steps/s (KS-matched) vs plain FP64; serve p50
 WORKLOAD = dict(n_species=32, n_reactions=64, n_sims=65536, t_end=100.0, n_samples=101,
                 x0_max=1000, eps=0.03, n_c=10, max_attempts=1 << 20, network_seed=0)
 L2_FLUSH_BYTES = 256 << 20
-KERNEL_NAMES = {0: "lane_kernel<RefArith, false>", 1: "warp_f64_kernel", 2: "lane_kernel<RefArith, false>"}
+def kernel_name(args):
+    """The simulation kernel a headline launch runs."""
+    if args.layout == 1:
+        return "warp_f64_kernel"
+    arith = "RefArith" if args.precision == "fp64" else "FastArith"
+    return f"lane_kernel<{arith}, {'true' if args.schedule == 'multi' else 'false'}>"
 
 
-def algorithmic_fp64_ops(stats, M, N, nnz):
-    """FP64 operations the method performs, from the per-simulation counters.
+def propensity_ops(net):
+    """FP64 multiplies of one evaluation of all M propensities: c (order 0),
+    c*x (X), (c*x)*y (X+Y), c*h (2X)."""
+    ops = 0
+    for row in net.reactants:
+        order = sum(c for _, c in row)
+        ops += 0 if order == 0 else (2 if len(row) == 2 else 1)
+    return ops
 
-    Per SSA event: propensities (1.25 M mults), slot sums (M adds), slot tree
-    (31 adds), ln u (30 ops incl. one division), tau division, clock add,
-    target mult and ~2.5 descent subtractions: 2.25 M + 67.
-    Per leap attempt: propensities 1.25 M, a0 and a0c (2 M + 62), mu/sigma^2
-    (4 per net-change entry), tau' (~7 per species), tau'' (31), and M Poisson
-    draws at ~40 ops (inversion path): 43.25 M + 4 nnz + 7 N + 93.
-    """
+
+def algorithmic_fp64_ops(stats, work, net):
+    """FP64 operations of the method (CGP 2006 tau-leaping with the CGP 2005
+    critical set and exact-SSA blocks), from the launch's counters.
+
+    Counters: ssa_steps and leap attempts (leaps + rejected) from the
+    per-simulation stats; the rest from ssa_options.work_counters.  Per unit:
+      SSA event: the M propensities (P multiplies) and the O(M) selection
+        (M/32 + 5 adds/compares), -ln u (22), tau = E/a0 (1), the clock (1)
+        and the target u a0 (1): P + M/32 + 30;
+      step selection: propensities P, the a0 and a0c sums (2M), the
+        fallback threshold a0 division (1);
+      tau' term (one reaction's contribution to mu_i and sigma_i^2): 2
+        products and 2 adds; tau' species: eps x / g and the clamp (2), two
+        divisions and bound^2 (3);
+      leap attempt: the step choice and clock (2); tau'' evaluation: -ln u
+        and the division (23); Poisson mean a_j tau: 1;
+      inversion draw: e^-lam (17) + the first term (1), 3 per further term;
+      PTRS draw: sqrt and the constants b, a, v_r (8); iteration: the
+        candidate (2a/us + b) U + lam + 0.43 and the squeeze (6); acceptance
+        test: two logarithms and ln k! (~70).
+    Langevin increments are not counted (tau-leap mode has none)."""
+    M = net.n_reactions
+    P = propensity_ops(net)
     ssa = float(stats["ssa_steps"].sum())
-    leap_attempts = float(stats["leaps"].sum() + stats["rejected"].sum())
-    return ssa * (2.25 * M + 67) + leap_attempts * (43.25 * M + 4 * nnz + 7 * N + 93)
+    attempts = float(stats["leaps"].sum() + stats["rejected"].sum())
+    w = {name: float(work[k]) for k, name in enumerate(
+        ("selections", "tau_terms", "tau_species", "tau2", "means", "inv_draws", "inv_terms", "ptrs_draws",
+         "ptrs_iters", "ptrs_tests"))}
+    return (ssa * (P + M / 32 + 30) + w["selections"] * (P + 2 * M + 1) + 4 * w["tau_terms"]
+            + 5 * w["tau_species"] + 2 * attempts + 23 * w["tau2"] + w["means"] + 18 * w["inv_draws"]
+            + 3 * w["inv_terms"] + 8 * w["ptrs_draws"] + 6 * w["ptrs_iters"] + 70 * w["ptrs_tests"])
 
 
 class ClockSampler:
@@ -261,31 +295,36 @@ def run_hetero(args):
                                    f"species = reactions/2), replicates logU[16,8192], t_end logU[10,1000], 101 samples",
                        "n_sims": sum(int(g['params'].shape[0]) for g in gd), "max_attempts": cap,
                        "schedule": f"autotuned: most expensive group first, block_warps={topts.block_warps}, "
-                                   f"sims_per_warp={topts.sims_per_warp}"}}
+                                   f"sims_per_warp={topts.sims_per_warp}, reg_cap={topts.reg_cap}"}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_served(args):
-    """Served request stream: Poisson arrivals, continuous batching, p50/p99."""
+def served_stream(rates, n_requests, n_networks, cap, seed=7, n_streams=4, max_batch=16):
+    """Served request stream (continuous batching through abi.Server): a pool
+    of random networks (M logU-int[8,512], N U-int[4,min(256,2M)]); per
+    request a network from the pool, replicates logU-int[1,4096], t_end
+    logU[1,500], S U-int[10,200] sample times, rates logU[1e-4,1], x0
+    U{0..1000}; Poisson arrivals at each rate.  Fast mode.  Returns one dict
+    per rate: p50/p99/mean latency (submit to completion), firings/s and
+    sim-steps/s over the rate's wall time, launches and mean batch size."""
     import torch  # noqa: F401  (initialises the CUDA context used by the server)
 
     from paper_1309_7695_b300 import abi
 
-    rng = np.random.default_rng(7)
+    rng = np.random.default_rng(seed)
     pool = []
-    for k in range(args.serve_networks):
+    for k in range(n_networks):
         m = int(np.floor(np.exp(rng.uniform(np.log(8), np.log(513)))))
         n = int(rng.integers(4, min(256, 2 * m) + 1))
         net = inputs.random_network(n, m, 500 + k)
         pool.append((net, abi.Model(net)))
-    cap = args.serve_cap
     opts = abi.ssa_default_options(precision=abi.SSA_FAST, max_attempts=cap)
     results = []
-    for lam in args.serve_rates:
-        srv = abi.Server(n_streams=4, max_batch=16, opts=opts)
+    for lam in rates:
+        srv = abi.Server(n_streams=n_streams, max_batch=max_batch, opts=opts)
         reqs = []
-        for r in range(args.serve_requests):
+        for r in range(n_requests):
             net, model = pool[int(rng.integers(len(pool)))]
             reps = int(np.floor(np.exp(rng.uniform(0.0, np.log(4097)))))
             t_end = float(np.exp(rng.uniform(0.0, np.log(500.0))))
@@ -296,12 +335,12 @@ def run_served(args):
         gaps = rng.exponential(1.0 / lam, size=len(reqs))
         t_start = time.perf_counter()
         tickets, next_t = [], 0.0
-        for (model, params, x0, t_end, T, seed), gap in zip(reqs, gaps):
+        for (model, params, x0, t_end, T, sd), gap in zip(reqs, gaps):
             next_t += gap
             delay = next_t - (time.perf_counter() - t_start)
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(srv.submit(model, params, x0, t_end, T, seed))
+            tickets.append(srv.submit(model, params, x0, t_end, T, sd))
         lat, fir, steps, bsz = [], 0.0, 0.0, []
         for t in tickets:
             info = srv.wait(t)
@@ -317,15 +356,28 @@ def run_served(args):
         results.append({"lambda_per_s": lam, "requests": len(reqs), "p50_s": float(np.percentile(lat, 50)),
                         "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
                         "firings_per_s": fir / wall, "sim_steps_per_s": steps / wall, "wall_s": wall,
-                        "launches": launches, "mean_batch": float(np.mean(bsz))})
+                        "requests_per_s": len(reqs) / wall, "launches": launches, "mean_batch": float(np.mean(bsz))})
+    for _, model in pool:
+        model.close()
+    return results
+
+
+def served_config(n_requests, n_networks, cap):
+    return {"workload": f"served stream: Poisson arrivals, {n_requests} requests per rate, pool of {n_networks} random "
+                        f"networks (M logU-int[8,512], N U-int[4,min(256,2M)]), replicates logU-int[1,4096], "
+                        f"t_end logU[1,500], S U-int[10,200]", "max_attempts": cap,
+            "server": "4 stream slots, 16 per batch, per-request completion"}
+
+
+def run_served(args):
+    """Served request stream: Poisson arrivals, continuous batching, p50/p99."""
+    results = []
+    for lam in args.serve_rates:
+        results += served_stream([lam], args.serve_requests, args.serve_networks, args.serve_cap)
         print(json.dumps({"served": results[-1]}), flush=True)
     line = {"metric": METRIC, "workload": "served", "value": results[0]["p99_s"], "unit": "s (p99 latency)",
             "higher_is_better": False, "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'", "data": "synthetic",
-            "rates": results,
-            "config": {"workload": f"served stream: Poisson arrivals, {args.serve_requests} requests per rate, "
-                                   f"pool of {args.serve_networks} random networks (M logU-int[8,512], "
-                                   f"N U-int[4,min(256,2M)]), replicates logU-int[1,4096], t_end logU[1,500], "
-                                   f"S U-int[10,200]", "max_attempts": cap, "server": "4 stream slots, 16 per batch"}}
+            "rates": results, "config": served_config(args.serve_requests, args.serve_networks, args.serve_cap)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -398,16 +450,18 @@ def run_rre(args):
     accepted = float(s["leaps"].sum()) * args.steps
     ops = attempts * rre_fp64_ops_per_attempt(net)
     achieved = ops / dt
+    peak, rates = measured_fp64_peak()
     line = {"metric": "RRE integration attempts/s (Dormand-Prince 5(4), FP64, bit-exact with the oracle)",
             "workload": "rre", "value": attempts / dt, "unit": "attempts/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "accepted_steps_per_s": accepted / dt, "systems_per_s": n * args.steps / dt,
             "dtype": "f64", "data": "synthetic (seeded random network and parameter sweep)",
             "status_ok": int((s["status"] == 0).sum()), "max_attempts_one_system": int(s["attempts"].max()),
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
-                         "unit": "T FP64-op/s", "frac": achieved / FP64_PEAK_OPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                         "unit": "T FP64-op/s", "frac": achieved / peak, "traffic": None,
                          "ops_per_attempt": rre_fp64_ops_per_attempt(net),
-                         "peak_source": "nominal B300 FP64 1.25 TFLOP/s, a multiply-add counted once"},
+                         "peak_source": "of measured: FP64 add rate of this device (ssa_measure_issue_rates, live)",
+                         "nominal_frac": achieved / FP64_NOMINAL_OPS},
             "gpu_launches": args.steps, "clocks": clk,
             "config": {"workload": f"RRE of a random mass-action network 32 species x 64 reactions, {n} parameter "
                                    f"sets (rates logU[1e-4,1], x0 U{{0..1000}}), t_end={args.rre_t_end:g}, {S} sample "
@@ -478,9 +532,20 @@ def run_cle(args):
     return 0
 
 
-# FP64 peak: the nominal B300 FP64 rate, 1.25 TFLOP/s, as FP64 operations with
-# a multiply-add counted once (the unit of the algorithmic counts above)
-FP64_PEAK_OPS = 1.25e12 / 2
+# FP64 peak for context: the nominal B300 FP64 rate, 1.25 TFLOP/s, as FP64
+# operations with a multiply-add counted once
+FP64_NOMINAL_OPS = 1.25e12 / 2
+
+
+def measured_fp64_peak():
+    """The device's FP64 add rate, measured live by the library's issue-rate
+    microbenchmark (ssa_measure_issue_rates: a full-device grid of
+    independent add chains, best of three launches): the roofline
+    denominator of kernels bound by FP64 instruction issue."""
+    from paper_1309_7695_b300 import abi
+
+    r = abi.ssa_measure_issue_rates()
+    return r["fp64_adds_per_s"], r
 
 
 def main():
@@ -490,13 +555,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--layout", type=int, default=0, help="0 auto, 1 warp per simulation, 2 lane per simulation")
-    ap.add_argument("--schedule", default="streams", choices=["multi", "streams", "serial"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fast"],
+                    help="precision of the headline leg (fp64: the reference mode, the reported benchmark)")
+    ap.add_argument("--schedule", default="multi", choices=["multi", "streams", "serial"],
                     help="multi: the steps' batches in flight in one persistent launch; streams: one launch per "
                          "batch on its own stream; serial: one launch per batch, one after another")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fast", action="store_true")
     ap.add_argument("--no-moments", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--side-batches", type=int, default=8,
+                    help="batches simulated by each side leg (fast, persistent, moments, end to end)")
+    ap.add_argument("--served-rate", type=float, default=0.5, help="arrival rate of the short served leg (1/s)")
+    ap.add_argument("--served-requests", type=int, default=32)
     # profiling / sweep knobs; the reported benchmark uses the defaults
     ap.add_argument("--sims", type=int, default=None, help="override the simulations per GPU (profiling)")
     ap.add_argument("--cap", type=int, default=None, help="override the per-simulation attempt cap (profiling)")
@@ -546,30 +618,35 @@ def main():
     batch = make_batch(rank)
     net = batch.network
     N, M, S, n = net.n_species, net.n_reactions, len(batch.sample_times), batch.n_sims
-    nnz = int((net.stoichiometry() != 0).sum())
     sim_offset = shard.weak_offset(rank, n)
     model = abi.Model(net)
     p = torch.from_numpy(batch.params).to(dev)
     x = torch.from_numpy(batch.x0).to(dev)
     T = torch.from_numpy(batch.sample_times).to(dev)
+    # the side legs (fast mode, persistent, moments, end to end) simulate at
+    # most this many batches, so that the whole run stays within minutes
+    side_k = min(args.steps, args.side_batches)
     nb = max(args.steps, args.warmup) if args.schedule != "serial" else 1
+    nb = max(nb, side_k)
     outs = [torch.empty((n, S, N), dtype=torch.int32, device=dev) for _ in range(nb)]
     sts = [torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev) for _ in range(nb)]
+    work = torch.zeros(abi.SSA_WORK_COUNTERS, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    side = [torch.cuda.Stream(device=dev) for _ in range(nb)] if args.schedule == "streams" else []
+    side = [torch.cuda.Stream(device=dev) for _ in range(nb)]
 
-    def options(precision):
+    def options(precision, counted=False):
         return abi.ssa_default_options(eps=WORKLOAD["eps"], n_c=WORKLOAD["n_c"],
-                                       max_attempts=WORKLOAD["max_attempts"], layout=args.layout, precision=precision)
+                                       max_attempts=WORKLOAD["max_attempts"], layout=args.layout, precision=precision,
+                                       work_counters=work.data_ptr() if counted else None)
 
-    def run(seeds, precision):
+    def run(seeds, precision, schedule, counted=False):
         """Simulate one batch per seed (the steps); returns (seconds, [stats], launches)."""
-        o = options(precision)
+        o = options(precision, counted)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stats, launches = [], 0
-        if args.schedule == "multi":
+        if schedule == "multi":
             groups = [dict(model=model, params=p, x0=x, sample_times=T, samples=outs[k], stats=sts[k],
                            t_end=batch.t_end, seed=sd, sim_offset=sim_offset) for k, sd in enumerate(seeds)]
             e0.record(stream)
@@ -579,7 +656,7 @@ def main():
             torch.cuda.synchronize()
             dt = e0.elapsed_time(e1) / 1e3
             stats = [sts[k].cpu().numpy().view(abi.STATS_DTYPE).reshape(-1) for k in range(len(seeds))]
-        elif args.schedule == "streams":
+        elif schedule == "streams":
             e0.record(stream)
             for k, sd in enumerate(seeds):
                 side[k].wait_event(e0)
@@ -606,45 +683,83 @@ def main():
                 launches += 1
         return dt, stats, launches
 
-    peak_ops = FP64_PEAK_OPS
-    run([5000 + w for w in range(args.warmup)], abi.SSA_FP64_REF)
+    def sched_name(schedule):
+        return {"multi": f"the {args.steps} steps' batches in flight in one persistent launch",
+                "streams": f"one launch per step on {args.steps} concurrent streams",
+                "serial": "one launch per step, one after another, L2 flushed between"}[schedule]
 
+    def totals(stats):
+        fir = sum(float(s["firings"].sum()) for s in stats)
+        steps = sum(float(s["leaps"].sum() + s["ssa_steps"].sum()) for s in stats)
+        return fir, steps
+
+    head_prec = abi.SSA_FP64_REF if args.precision == "fp64" else abi.SSA_FAST
+    run([5000 + w for w in range(args.warmup)], head_prec, args.schedule)
+    peak_ops, issue_rates = measured_fp64_peak()
+
+    # ---- the headline: FP64 reference mode, K batches (work counted in the same launches)
     clocks = ClockSampler(local)
     flush.fill_(1)
+    work.zero_()
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    local_t, stats, launches = run([1000 + k for k in range(args.steps)], abi.SSA_FP64_REF)
+    local_t, stats, launches = run([1000 + k for k in range(args.steps)], head_prec, args.schedule, counted=True)
     clk = clocks.stop()
     barrier()
-    fir = sum(float(s["firings"].sum()) for s in stats)
-    simsteps = sum(float(s["leaps"].sum() + s["ssa_steps"].sum()) for s in stats)
-    ops = sum(algorithmic_fp64_ops(s, M, N, nnz) for s in stats)
+    fir, simsteps = totals(stats)
+    wk = work.cpu().numpy().astype(np.float64)
+    ops = sum(algorithmic_fp64_ops(s, wk / len(stats), net) for s in stats)
     capped = sum(int((s["status"] == abi.SSA_STATUS_STEP_LIMIT).sum()) for s in stats)
     t_max, (fir, simsteps, ops, capped) = shard.reduce_run(local_t, [fir, simsteps, ops, capped], device=dev)
 
-    fast = None
+    # ---- the spec comparison: the plain one-launch-per-batch FP64 kernel against the
+    # fast form in one persistent launch (the fast form's accuracy against FP64: the coupled
+    # KS / moment tests)
+    plain = None
     if not args.no_fast:
-        # the same batches in fast mode (FP32 propensities and Poisson sampler; its accuracy
-        # against the FP64 mode is established by the coupled KS / moment tests)
-        ft, fstats, _ = run([1000 + k for k in range(args.steps)], abi.SSA_FAST)
-        ff = sum(float(s["firings"].sum()) for s in fstats)
-        fsteps = sum(float(s["leaps"].sum() + s["ssa_steps"].sum()) for s in fstats)
+        pt, pstats, _ = run([3000], abi.SSA_FP64_REF, "serial")
+        pf, ps = totals(pstats)
+        pt, (pf, ps) = shard.reduce_run(pt, [pf, ps], device=dev)
+        plain = {"value": pf / pt, "unit": "firings/s", "sim_steps_per_s": ps / pt, "seconds_per_batch": pt,
+                 "schedule": "one batch, one launch, L2 flushed before it"}
+    fast = None
+    fast_persistent = None
+    if not args.no_fast:
+        # fast mode on the headline's batches and schedule, for the precision comparison
+        ft, fstats, _ = run([1000 + k for k in range(args.steps)], abi.SSA_FAST, args.schedule)
+        ff, fsteps = totals(fstats)
         ft, (ff, fsteps) = shard.reduce_run(ft, [ff, fsteps], device=dev)
-        fast = {"value": ff / ft, "unit": "firings/s", "sim_steps_per_s": fsteps / ft, "ms_per_step": ft * 1e3 / args.steps,
+        fast = {"value": ff / ft, "unit": "firings/s", "sim_steps_per_s": fsteps / ft,
+                "ms_per_step": ft * 1e3 / args.steps, "batches": args.steps, "schedule": sched_name(args.schedule),
                 "vs_fp64": (ff / ft) / (fir / t_max), "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'"}
+        seeds = [1000 + k for k in range(side_k)]
+        work.zero_()
+        mt, mstats, _ = run(seeds, abi.SSA_FAST, "multi", counted=True)
+        mf, msteps = totals(mstats)
+        mwk = work.cpu().numpy().astype(np.float64)
+        mops = sum(algorithmic_fp64_ops(s, mwk / len(mstats), net) for s in mstats)
+        mt, (mf, msteps, mops) = shard.reduce_run(mt, [mf, msteps, mops], device=dev)
+        fast_persistent = {"value": mf / mt, "unit": "firings/s", "sim_steps_per_s": msteps / mt,
+                           "ms_per_step": mt * 1e3 / side_k, "batches": side_k,
+                           "schedule": f"the {side_k} batches in one persistent launch",
+                           "vs_plain_fp64": (mf / mt) / plain["value"] if plain else None,
+                           "roofline": {"bound": "alu", "achieved": mops / mt / 1e12, "peak": peak_ops / 1e12,
+                                        "unit": "T FP64-op/s (method ops at FP64 rate)",
+                                        "frac": mops / mt / peak_ops, "peak_source": "of measured (live)"},
+                           "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'"}
 
     moments = None
-    if not args.no_moments and args.schedule == "streams":
+    if not args.no_moments:
         # the same batches with sweep moments accumulated on the device instead of
-        # trajectories written (ssa_simulate_moments_dev), K batches in flight
+        # trajectories written (ssa_simulate_moments_dev), batches in flight on streams
         o = options(abi.SSA_FP64_REF)
-        means = [torch.empty((S, N), dtype=torch.float64, device=dev) for _ in range(args.steps)]
-        varis = [torch.empty((S, N), dtype=torch.float64, device=dev) for _ in range(args.steps)]
+        means = [torch.empty((S, N), dtype=torch.float64, device=dev) for _ in range(side_k)]
+        varis = [torch.empty((S, N), dtype=torch.float64, device=dev) for _ in range(side_k)]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for k in range(args.steps):
+        for k in range(side_k):
             side[k].wait_event(e0)
             abi.ssa_simulate_moments_dev(model, p, x, batch.t_end, T, means[k], varis[k], sts[k], seed=1000 + k,
                                          opts=o, sim_offset=sim_offset, stream=side[k])
@@ -652,10 +767,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         mt = e0.elapsed_time(e1) / 1e3
-        mf = sum(float(sts[k].cpu().numpy().view(abi.STATS_DTYPE)["firings"].sum()) for k in range(args.steps))
+        mf = sum(float(sts[k].cpu().numpy().view(abi.STATS_DTYPE)["firings"].sum()) for k in range(side_k))
         mt, (mf,) = shard.reduce_run(mt, [mf], device=dev)
-        moments = {"value": mf / mt, "unit": "firings/s", "ms_per_step": mt * 1e3 / args.steps,
-                   "vs_trajectories": (mf / mt) / (fir / t_max),
+        moments = {"value": mf / mt, "unit": "firings/s", "ms_per_step": mt * 1e3 / side_k, "batches": side_k,
                    "output_bytes_per_step": int(2 * S * N * 8), "trajectory_bytes_per_step": int(n * S * N * 4)}
 
     e2e = None
@@ -665,13 +779,13 @@ def main():
         hp = torch.from_numpy(batch.params).pin_memory().numpy()
         hx = torch.from_numpy(batch.x0).pin_memory().numpy()
         hT = batch.sample_times.copy()
-        hs = [torch.empty((n, S, N), dtype=torch.int32).pin_memory().numpy() for _ in range(args.steps)]
-        hst = [np.zeros(n, dtype=abi.STATS_DTYPE) for _ in range(args.steps)]
+        hs = [torch.empty((n, S, N), dtype=torch.int32).pin_memory().numpy() for _ in range(side_k)]
+        hst = [np.zeros(n, dtype=abi.STATS_DTYPE) for _ in range(side_k)]
         o = options(abi.SSA_FP64_REF)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        jobs = [abi.ssa_submit_batch(model, hp, hx, batch.t_end, hT, seed=1000 + k, opts=o) for k in range(args.steps)]
+        jobs = [abi.ssa_submit_batch(model, hp, hx, batch.t_end, hT, seed=1000 + k, opts=o) for k in range(side_k)]
         for k, job in enumerate(jobs):
             job.fetch(hs[k], hst[k])
         e2e_t = time.perf_counter() - t0
@@ -679,33 +793,44 @@ def main():
             job.release()
         e2e_f = sum(float(h["firings"].sum()) for h in hst)
         e2e_t, (e2e_f,) = shard.reduce_run(e2e_t, [e2e_f], device=dev)
-        e2e = {"value": e2e_f / e2e_t, "unit": "firings/s",
+        e2e = {"value": e2e_f / e2e_t, "unit": "firings/s", "batches": side_k,
                "h2d_bytes_per_step": int(hp.nbytes + hx.nbytes + hT.nbytes),
                "d2h_bytes_per_step": int(hs[0].nbytes + hst[0].nbytes),
                "schedule": "one ssa_submit_batch job (own stream) per step, all in flight"}
 
+    served = None
+    if not args.no_served and world == 1:
+        res = served_stream([args.served_rate], args.served_requests, args.serve_networks, args.serve_cap)[0]
+        served = {**res, "config": served_config(args.served_requests, args.serve_networks, args.serve_cap),
+                  "note": "arrival rate chosen below the measured service capacity of this stream"}
+
     if rank == 0:
         kernel_s = local_t / launches
         achieved = ops / world / launches / kernel_s
-        sched = {"multi": f"the {args.steps} steps' batches in flight in one persistent launch",
-                 "streams": f"one launch per step on {args.steps} concurrent streams",
-                 "serial": "one launch per step, one after another, L2 flushed between"}[args.schedule]
+        sched = sched_name(args.schedule)
         line = {"metric": METRIC, "value": fir / t_max, "unit": "firings/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32 propensities/Poisson, f64 clock/a0/tau'",
                 "data": "synthetic (seeded random network and parameter sweep)",
                 "sim_steps_per_s": simsteps / t_max,
                 "config": config_dict({"parallelism": f"dp{world} (independent simulation shards)",
+                                       "precision": "fp64-ref" if args.precision == "fp64" else "fast",
                                        "capped_fraction": capped / (world * n * args.steps), "schedule": sched,
                                        "l2": "each step reads 41 MB of inputs and writes 847 MB of samples (> L2); "
                                              "L2 flushed before the timed region"}),
                 "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                              "unit": "T FP64-op/s", "frac": achieved / peak_ops, "traffic": None,
-                             "kernel": ("lane_kernel<RefArith, true>" if args.schedule == "multi"
-                                        else KERNEL_NAMES.get(args.layout, "lane_kernel<RefArith, false>")),
-                             "peak_source": "nominal B300 FP64 1.25 TFLOP/s, one operation per multiply-add "
-                                            "(of nominal; the measured scalar FP64 issue rate is 0.46 T op/s)"},
-                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "fast_mode": fast, "moments_mode": moments}
+                             "kernel": kernel_name(args),
+                             "peak_source": "of measured: FP64 add rate of this device, measured live by "
+                                            "ssa_measure_issue_rates",
+                             "nominal_frac": achieved / FP64_NOMINAL_OPS,
+                             "fp32_adds_per_s": issue_rates["fp32_adds_per_s"],
+                             "fp64_add_latency_cycles": issue_rates["fp64_add_latency_cycles"],
+                             "ops_per_batch": ops / (world * args.steps),
+                             "work_counters_per_batch": {nm: float(v) / args.steps for nm, v in zip(abi.WORK_NAMES, wk)}},
+                "clocks": clk, "gpu_launches": launches, "e2e": e2e, "plain_fp64": plain, "fast_mode": fast,
+                "fast_persistent": fast_persistent, "served": served, "moments_mode": moments}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_rate(batch)
         print(json.dumps(line), flush=True)
@@ -713,7 +838,6 @@ def main():
         dist.destroy_process_group()
     model.close()
     return 0
-
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -117,7 +117,34 @@ typedef struct {
     int32_t ctas_per_sm;   /* lane layout: resident CTAs per SM (0 = as many as fit); with fewer, the
                               shared-memory carve-out is sized to them and the rest of each SM's
                               on-chip memory serves as L1 cache for the rate constants */
+    int32_t reg_cap;       /* lane layout: register budget of the kernel build: 0 = up to 255 registers per
+                              thread, 1 = the build limited to 168 so that three CTAs of at most 4 warps
+                              fit per SM when shared memory allows (block_warps must be <= 4) */
+    uint64_t *work_counters; /* optional DEVICE array of SSA_WORK_COUNTERS uint64 that the launch adds
+                                its work to (lane layout, tau-leaping modes; see below); NULL = none */
 } ssa_options;
+
+/* Work the method performed in a launch, for measurement (ssa_options.
+ * work_counters; the counts are added to the array, which the caller
+ * clears).  Exact SSA events and leap attempts are in ssa_sim_stats.
+ * Counted: step selections (propensities, a0, critical set and tau' of a
+ * state; CGP 2006), terms of the mu / sigma^2 sums of the species that bound
+ * tau' and those species, tau'' evaluations (attempts with a critical
+ * reaction), Poisson means formed (noncritical reactions per attempt),
+ * inversion draws and the sum of their results (cdf terms after the first),
+ * PTRS draws, their iterations and their acceptance tests after the
+ * squeeze (Hormann 1993).  Langevin increments are not counted. */
+#define SSA_WORK_SELECTIONS 0
+#define SSA_WORK_TAU_TERMS 1
+#define SSA_WORK_TAU_SPECIES 2
+#define SSA_WORK_TAU2 3
+#define SSA_WORK_MEANS 4
+#define SSA_WORK_INV_DRAWS 5
+#define SSA_WORK_INV_TERMS 6
+#define SSA_WORK_PTRS_DRAWS 7
+#define SSA_WORK_PTRS_ITERS 8
+#define SSA_WORK_PTRS_TESTS 9
+#define SSA_WORK_COUNTERS 10
 
 /* Per-simulation counters and status (56 bytes). */
 typedef struct {
@@ -186,6 +213,26 @@ int ssa_simulate_moments_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offs
                              const double *sample_times, int32_t n_samples, uint64_t seed,
                              const ssa_options *opts, double *mean, double *var, ssa_sim_stats *stats,
                              void *stream);
+
+/* Sweep histograms instead of trajectories (the same sweep post-processing):
+ * simulates like ssa_simulate_dev (same arguments, same random streams, lane
+ * layout) but writes no samples array; every recorded count x of sample k,
+ * species i adds 1 to one bin of the cell's histogram:
+ *   counts[k][i][0]          x < bin_lo (underflow),
+ *   counts[k][i][1 + b]      bin_lo + b bin_width <= x < bin_lo + (b+1) bin_width,
+ *                            b = 0..n_bins-1,
+ *   counts[k][i][n_bins + 1] x >= bin_lo + n_bins bin_width (overflow).
+ * counts is a DEVICE array [n_samples][N][n_bins + 2] of uint64, caller-owned;
+ * the launch ADDS to it (zero it first, or accumulate several batches), so
+ * every cell's bins sum to the simulations recorded into it.  The counts are
+ * exact integers whatever order simulations finish in.  SSA_EINVAL for
+ * n_bins < 1, bin_width < 1, n_samples < 1, a null counts array or more
+ * than 2^34 bins; SSA_EUNSUPPORTED with the warp layout. */
+int ssa_simulate_histograms_dev(ssa_model_t model, int64_t n_sims, int64_t sim_offset,
+                                const double *params, const int32_t *x0, double t_end,
+                                const double *sample_times, int32_t n_samples, uint64_t seed,
+                                const ssa_options *opts, int32_t bin_lo, int32_t bin_width, int32_t n_bins,
+                                uint64_t *counts, ssa_sim_stats *stats, void *stream);
 
 /* Deterministic counterpart of a sweep: the reaction-rate equations (the
  * paper's Methods section: for abundant species the state follows

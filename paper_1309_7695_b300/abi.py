@@ -42,9 +42,24 @@ SSA_LAYOUT_AUTO = 0
 SSA_LAYOUT_WARP = 1
 SSA_LAYOUT_LANE = 2
 
+# indices of ssa_options.work_counters
+SSA_WORK_SELECTIONS = 0
+SSA_WORK_TAU_TERMS = 1
+SSA_WORK_TAU_SPECIES = 2
+SSA_WORK_TAU2 = 3
+SSA_WORK_MEANS = 4
+SSA_WORK_INV_DRAWS = 5
+SSA_WORK_INV_TERMS = 6
+SSA_WORK_PTRS_DRAWS = 7
+SSA_WORK_PTRS_ITERS = 8
+SSA_WORK_PTRS_TESTS = 9
+SSA_WORK_COUNTERS = 10
+WORK_NAMES = ("selections", "tau_terms", "tau_species", "tau2", "means", "inv_draws", "inv_terms", "ptrs_draws",
+              "ptrs_iters", "ptrs_tests")
+
 EXPORTED = [
     "ssa_default_options", "ssa_load_model", "ssa_free_model", "ssa_model_info",
-    "ssa_simulate_dev", "ssa_simulate_moments_dev", "ssa_integrate_rre_dev", "ssa_simulate_dev_noalloc", "ssa_simulate_multi_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
+    "ssa_simulate_dev", "ssa_simulate_moments_dev", "ssa_simulate_histograms_dev", "ssa_integrate_rre_dev", "ssa_simulate_dev_noalloc", "ssa_simulate_multi_dev", "ssa_submit_batch", "ssa_poll", "ssa_wait", "ssa_fetch",
     "ssa_release_job", "ssa_last_error", "ssa_abi_version",
     "ssa_server_default_config", "ssa_server_create", "ssa_server_submit", "ssa_server_poll", "ssa_server_wait",
     "ssa_server_fetch", "ssa_server_stats", "ssa_server_destroy", "ssa_server_last_error",
@@ -93,6 +108,7 @@ class Options(ctypes.Structure):
         ("n_c", ctypes.c_int32), ("ssa_block", ctypes.c_int32), ("ssa_factor", ctypes.c_double),
         ("max_halvings", ctypes.c_int32), ("layout", ctypes.c_int32), ("max_attempts", ctypes.c_int64),
         ("block_warps", ctypes.c_int32), ("sims_per_warp", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+        ("reg_cap", ctypes.c_int32), ("work_counters", ctypes.c_void_p),
     ]
 
 
@@ -139,6 +155,8 @@ def lib():
     L.ssa_simulate_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp, vp, vp]
     L.ssa_simulate_dev_noalloc.argtypes = L.ssa_simulate_dev.argtypes
     L.ssa_integrate_rre_dev.argtypes = [vp, i64, vp, vp, vp, i32, f64, f64, i64, vp, vp, vp]
+    L.ssa_simulate_histograms_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), i32,
+                                              i32, i32, vp, vp, vp]
     L.ssa_simulate_moments_dev.argtypes = [vp, i64, i64, vp, vp, f64, vp, i32, u64, ctypes.POINTER(Options), vp, vp,
                                            vp, vp]
     L.ssa_simulate_multi_dev.argtypes = [i32, ctypes.POINTER(Group), ctypes.POINTER(Options), vp]
@@ -261,6 +279,24 @@ def ssa_simulate_dev(model: Model, params, x0, t_end, sample_times, samples, sta
     _check(lib().ssa_simulate_dev(model.handle, n, int(sim_offset), _ptr(params), _ptr(x0), float(t_end),
                                   _ptr(sample_times), int(sample_times.numel()), int(seed), ctypes.byref(o),
                                   _ptr(samples), _ptr(stats), ctypes.c_void_p(int(handle))))
+
+
+def ssa_simulate_histograms_dev(model: Model, params, x0, t_end, sample_times, counts, bin_lo, bin_width, n_bins,
+                                stats=None, seed=0, opts=None, sim_offset=0, stream=None):
+    """Simulate like ssa_simulate_dev but only add every recorded count to its
+    (sample time, species) histogram: counts [S, N, n_bins + 2] int64 torch
+    CUDA tensor, added to (bin 0 underflow, bins 1..n_bins of width
+    bin_width from bin_lo, bin n_bins + 1 overflow)."""
+    n = int(params.shape[0]) if params.dim() == 2 else 0
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    o = opts if opts is not None else ssa_default_options()
+    _check(lib().ssa_simulate_histograms_dev(model.handle, n, int(sim_offset), _ptr(params), _ptr(x0), float(t_end),
+                                             _ptr(sample_times), int(sample_times.numel()), int(seed),
+                                             ctypes.byref(o), int(bin_lo), int(bin_width), int(n_bins), _ptr(counts),
+                                             _ptr(stats), ctypes.c_void_p(int(handle))))
 
 
 def ssa_simulate_moments_dev(model: Model, params, x0, t_end, sample_times, mean, var, stats=None, seed=0,

@@ -1,11 +1,13 @@
 """Launch-shape autotuner and multi-network scheduler.
 
-The kernels take three shape choices that change speed but never results:
+The kernels take four shape choices that change speed but never results:
 the layout (one simulation per lane for SSA steps with warp-cooperative
 leaps, or one warp per simulation), the warps per CTA (which sets shared
-memory per CTA and so occupancy), and how many lanes of a warp own a
+memory per CTA and so occupancy), how many lanes of a warp own a
 simulation (fewer spread heavy simulations over more warps, so their
-warp-cooperative leaps do not queue behind each other).  ``tune`` times
+warp-cooperative leaps do not queue behind each other), and the register
+budget of the kernel build (up to 255 registers per thread, or 168 so that
+a third 4-warp CTA fits on an SM when shared memory allows).  ``tune`` times
 short trial launches of the candidates on a strided sample of the batch
 (attempt cap lowered so a trial takes milliseconds) and keeps the fastest
 by attempts per second; results are cached per device and network shape.
@@ -28,7 +30,9 @@ import numpy as np
 from . import abi
 
 CACHE_ENV = "TAULEAP_TUNE_CACHE"
-LANE_CANDIDATES = [(2, 32), (4, 32), (8, 32), (4, 16), (4, 8), (8, 4)]
+# (warps per CTA, simulations per warp, register budget: 0 = up to 255, 1 = 168)
+LANE_CANDIDATES = [(2, 32, 0), (4, 32, 0), (8, 32, 0), (4, 16, 0), (4, 8, 0), (8, 4, 0), (4, 32, 1), (2, 32, 1),
+                   (4, 16, 1)]
 
 
 def _cache_path() -> str:
@@ -81,7 +85,7 @@ def _trial(model, p, x, T, t_end, opts, seed, torch):
 
 def tune(network, model, params, x0, sample_times, t_end, precision=abi.SSA_FP64_REF,
          mode=abi.SSA_MODE_TAU_LEAP, sample=2048, trial_cap=4096, seed=12345, use_cache=True):
-    """Pick (layout, block_warps, sims_per_warp) for one network.
+    """Pick (layout, block_warps, sims_per_warp, reg_cap) for one network.
 
     params/x0/sample_times: torch CUDA tensors of the batch (a strided
     sample of ``sample`` rows is timed).  Returns a dict with the chosen
@@ -96,20 +100,21 @@ def tune(network, model, params, x0, sample_times, t_end, precision=abi.SSA_FP64
     rows = torch.from_numpy(_sample_rows(int(params.shape[0]), sample)).to(params.device)
     p, x = params.index_select(0, rows).contiguous(), x0.index_select(0, rows).contiguous()
     results = []
-    cands = [(abi.SSA_LAYOUT_LANE, bw, spw) for bw, spw in LANE_CANDIDATES]
+    cands = [(abi.SSA_LAYOUT_LANE, bw, spw, rc) for bw, spw, rc in LANE_CANDIDATES]
     if precision == abi.SSA_FP64_REF:
-        cands.append((abi.SSA_LAYOUT_WARP, 4, 0))
-    for layout, bw, spw in cands:
+        cands.append((abi.SSA_LAYOUT_WARP, 4, 0, 0))
+    for layout, bw, spw, rc in cands:
         o = abi.ssa_default_options(precision=precision, mode=mode, max_attempts=trial_cap, layout=layout,
-                                    block_warps=bw, sims_per_warp=spw)
+                                    block_warps=bw, sims_per_warp=spw, reg_cap=rc)
         try:
             rate, dt = _trial(model, p, x, sample_times, t_end, o, seed, torch)
         except abi.SsaError:
             continue
-        results.append({"layout": layout, "block_warps": bw, "sims_per_warp": spw, "attempts_per_s": rate})
+        results.append({"layout": layout, "block_warps": bw, "sims_per_warp": spw, "reg_cap": rc,
+                        "attempts_per_s": rate})
     best = max(results, key=lambda r: r["attempts_per_s"])
     entry = {"layout": best["layout"], "block_warps": best["block_warps"], "sims_per_warp": best["sims_per_warp"],
-             "candidates": results}
+             "reg_cap": best["reg_cap"], "candidates": results}
     if use_cache:
         cache[key] = entry
         _store_cache(cache)
@@ -121,6 +126,7 @@ def apply(opts, entry):
     opts.layout = entry["layout"]
     opts.block_warps = entry["block_warps"]
     opts.sims_per_warp = entry["sims_per_warp"]
+    opts.reg_cap = entry.get("reg_cap", 0)
     return opts
 
 
@@ -147,7 +153,7 @@ def plan(groups, precision=abi.SSA_FAST, mode=abi.SSA_MODE_TAU_LEAP, sample=64, 
     ordered = [groups[k] for k in order]
     # launch shape for the mixed workload: trial on a strided subset of every group
     best, best_rate = None, -1.0
-    for bw, spw in LANE_CANDIDATES:
+    for bw, spw, rc in LANE_CANDIDATES:
         trial = []
         for g in ordered:
             n = int(g["params"].shape[0])
@@ -160,7 +166,7 @@ def plan(groups, precision=abi.SSA_FAST, mode=abi.SSA_MODE_TAU_LEAP, sample=64, 
                               stats=torch.empty((m, abi.STATS_DTYPE.itemsize), dtype=torch.uint8,
                                                 device=g["params"].device)))
         o = abi.ssa_default_options(precision=precision, mode=mode, max_attempts=trial_cap, block_warps=bw,
-                                    sims_per_warp=spw)
+                                    sims_per_warp=spw, reg_cap=rc)
         try:
             abi.ssa_simulate_multi_dev(trial, opts=o)
             torch.cuda.synchronize()
@@ -173,6 +179,7 @@ def plan(groups, precision=abi.SSA_FAST, mode=abi.SSA_MODE_TAU_LEAP, sample=64, 
         att = sum(float(t["stats"].cpu().numpy().view(abi.STATS_DTYPE)["attempts"].sum()) for t in trial)
         rate = att / max(dt, 1e-9)
         if rate > best_rate:
-            best, best_rate = (bw, spw), rate
-    opts = abi.ssa_default_options(precision=precision, mode=mode, block_warps=best[0], sims_per_warp=best[1])
+            best, best_rate = (bw, spw, rc), rate
+    opts = abi.ssa_default_options(precision=precision, mode=mode, block_warps=best[0], sims_per_warp=best[1],
+                                   reg_cap=best[2])
     return ordered, opts, [costs[k] for k in order]

@@ -197,7 +197,8 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
     L.off_dep_ptr = L.off_hor + N;
     L.off_dep_ent = L.off_dep_ptr + N + 1;
     L.off_cinfo = L.off_dep_ent + ndep;
-    L.words = L.off_cinfo + M;
+    L.off_dmask = L.off_cinfo + M;
+    L.words = L.off_dmask + M;
     L.max_nu_len = max_nu_len;
     std::vector<int32_t> blob(L.words);
     std::copy(rinfo.begin(), rinfo.end(), blob.begin() + L.off_rinfo);
@@ -231,6 +232,10 @@ int ssa_load_model(const ssa_model_desc *d, ssa_model_t *out)
             ++slot;
         }
         blob[L.off_cinfo + j] = (int32_t)ci;
+        uint32_t dm = 0;
+        for (int v : nu_rows[j])
+            for (int k : dep_rows[v >> 8]) dm |= 1u << (k & 31);
+        blob[L.off_dmask + j] = (int32_t)dm;
     }
 
     auto *m = new ssa_model();
@@ -288,6 +293,8 @@ static int check_options(const ssa_options *o)
     if (o->block_warps < 0 || o->block_warps > 8) return fail(SSA_EINVAL, "block_warps must be in 0..8");
     if (o->sims_per_warp < 0 || o->sims_per_warp > 32) return fail(SSA_EINVAL, "sims_per_warp must be in 0..32");
     if (o->ctas_per_sm < 0 || o->ctas_per_sm > 32) return fail(SSA_EINVAL, "ctas_per_sm must be in 0..32");
+    if (o->reg_cap != 0 && o->reg_cap != 1) return fail(SSA_EINVAL, "reg_cap must be 0 or 1");
+    if (o->reg_cap == 1 && o->block_warps > 4) return fail(SSA_EINVAL, "the 168-register build runs at most 4 warps per CTA");
     return SSA_OK;
 }
 
@@ -301,7 +308,9 @@ namespace {
 int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
                       const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
                       uint64_t seed, const ssa_options *opts, int32_t *samples, ssa_sim_stats *stats,
-                      void *stream, unsigned long long *counter_in, unsigned long long *moments = nullptr)
+                      void *stream, unsigned long long *counter_in, unsigned long long *moments = nullptr,
+                      unsigned long long *hist = nullptr, int32_t hist_lo = 0, int32_t hist_width = 1,
+                      int32_t hist_bins = 0)
 {
     if (!m) return fail(SSA_EINVAL, "null model");
     ssa_options o;
@@ -313,7 +322,7 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     if (n_samples < 0) return fail(SSA_EINVAL, "n_samples < 0");
     if (!(t_end >= 0.0) || !std::isfinite(t_end)) return fail(SSA_EINVAL, "t_end must be finite and >= 0");
     if (n_sims == 0) return SSA_OK;
-    if (!params || !x0 || (n_samples > 0 && (!sample_times || (!samples && !moments))))
+    if (!params || !x0 || (n_samples > 0 && (!sample_times || (!samples && !moments && !hist))))
         return fail(SSA_EINVAL, "null device array");
     DeviceGuard g(m->device);
     if (!g.ok) return fail(SSA_ECUDA, "cannot select the model's device");
@@ -326,8 +335,8 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     int layout = o.layout;
     if (layout == SSA_LAYOUT_AUTO)
         layout = (tl::lane_f64_smem_bytes(m->L, 1) <= (size_t)smem_optin) ? SSA_LAYOUT_LANE : SSA_LAYOUT_WARP;
-    if (moments && layout != SSA_LAYOUT_LANE)
-        return fail(SSA_EUNSUPPORTED, "sweep moments are accumulated by the lane layout only");
+    if ((moments || hist) && layout != SSA_LAYOUT_LANE)
+        return fail(SSA_EUNSUPPORTED, "sweep moments and histograms are accumulated by the lane layout only");
     if (o.mode == SSA_MODE_CLE && layout != SSA_LAYOUT_LANE)
         return fail(SSA_EUNSUPPORTED, "network too large for the lane layout, which Langevin increments need");
     auto smem_of = [&](int w) {
@@ -338,8 +347,9 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     const size_t smem = smem_of(warps);
     if (smem > (size_t)smem_optin) return fail(SSA_EUNSUPPORTED, "network too large for the shared-memory workspace");
     const bool fast = (o.precision == SSA_FAST);
+    const int rc_var = layout == SSA_LAYOUT_LANE ? o.reg_cap : 0;
     const int occ = layout == SSA_LAYOUT_LANE
-                        ? (fast ? tl::lane_fast_occupancy(warps, smem) : tl::lane_ref_occupancy(warps, smem))
+                        ? (fast ? tl::lane_fast_occupancy(warps, smem, rc_var) : tl::lane_ref_occupancy(warps, smem, rc_var))
                         : tl::warp_ref_occupancy(warps, smem);
     int per_sm = std::max(1, occ);
     int carveout = -1;   // the driver's default carve-out
@@ -371,16 +381,21 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     a.max_halvings = o.max_halvings;
     a.max_attempts = o.max_attempts;
     a.sims_per_warp = spw;
+    a.work = layout == SSA_LAYOUT_LANE ? reinterpret_cast<unsigned long long *>(o.work_counters) : nullptr;
     a.samples = samples;
     a.stats = stats;
     a.moments = moments;
+    a.hist = hist;
+    a.hist_lo = hist_lo;
+    a.hist_width = hist_width;
+    a.hist_bins = hist_bins;
     void *counter = counter_in;
     if (!counter_in) TL_CUDA(cudaMallocAsync(&counter, sizeof(unsigned long long), s));
     a.work_counter = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-        e = layout == SSA_LAYOUT_LANE ? (fast ? tl::launch_lane_fast(a, warps, grid, smem, carveout, s)
-                                              : tl::launch_lane_ref(a, warps, grid, smem, carveout, s))
+        e = layout == SSA_LAYOUT_LANE ? (fast ? tl::launch_lane_fast(a, warps, grid, smem, carveout, rc_var, s)
+                                              : tl::launch_lane_ref(a, warps, grid, smem, carveout, rc_var, s))
                                       : tl::launch_warp_ref(a, warps, grid, smem, s);
     cudaError_t e2 = counter_in ? cudaSuccess : cudaFreeAsync(counter, s);
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
@@ -498,6 +513,22 @@ int ssa_simulate_moments_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, 
     return SSA_OK;
 }
 
+int ssa_simulate_histograms_dev(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const double *params,
+                                const int32_t *x0, double t_end, const double *sample_times, int32_t n_samples,
+                                uint64_t seed, const ssa_options *opts, int32_t bin_lo, int32_t bin_width,
+                                int32_t n_bins, uint64_t *counts, ssa_sim_stats *stats, void *stream)
+{
+    g_error.clear();
+    if (!m) return fail(SSA_EINVAL, "null model");
+    if (n_bins < 1 || bin_width < 1) return fail(SSA_EINVAL, "n_bins and bin_width must be >= 1");
+    if (n_samples <= 0) return fail(SSA_EINVAL, "sweep histograms need at least one sample time");
+    if (!counts) return fail(SSA_EINVAL, "null counts array");
+    if ((long long)n_samples * m->L.N * (long long)(n_bins + 2) > (1ll << 34))
+        return fail(SSA_EINVAL, "too many histogram bins");
+    return simulate_dev_impl(m, n_sims, sim_offset, params, x0, t_end, sample_times, n_samples, seed, opts, nullptr,
+                             stats, stream, nullptr, nullptr, reinterpret_cast<unsigned long long *>(counts), bin_lo,
+                             bin_width, n_bins);
+}
 
 static void job_free_buffers(ssa_job *j)
 {
@@ -721,7 +752,8 @@ int simulate_multi_impl(int32_t n_groups, const ssa_group *groups, const ssa_opt
     while (warps > 1 && tl::lane_multi_smem_bytes(max_N, max_M, warps) > (size_t)smem_optin) --warps;
     const size_t smem = tl::lane_multi_smem_bytes(max_N, max_M, warps);
     if (smem > (size_t)smem_optin) return fail(SSA_EUNSUPPORTED, "largest network too large for the workspace");
-    const int occ = fast ? tl::lane_multi_fast_occupancy(warps, smem) : tl::lane_multi_ref_occupancy(warps, smem);
+    const int occ = fast ? tl::lane_multi_fast_occupancy(warps, smem, o.reg_cap)
+                         : tl::lane_multi_ref_occupancy(warps, smem, o.reg_cap);
     int per_sm = std::max(1, occ);
     int carveout = -1;
     if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) {
@@ -745,6 +777,7 @@ int simulate_multi_impl(int32_t n_groups, const ssa_group *groups, const ssa_opt
     a.max_halvings = o.max_halvings;
     a.max_attempts = o.max_attempts;
     a.sims_per_warp = spw;
+    a.work = reinterpret_cast<unsigned long long *>(o.work_counters);
     void *d_table = nullptr, *counter = nullptr;
     const size_t table_bytes = sizeof(tl::GroupArgs) * table.size();
     TL_CUDA(cudaMallocAsync(&d_table, table_bytes, s));
@@ -754,8 +787,8 @@ int simulate_multi_impl(int32_t n_groups, const ssa_group *groups, const ssa_opt
     if (e == cudaSuccess) {
         a.groups = static_cast<const tl::GroupArgs *>(d_table);
         a.work_counter = static_cast<unsigned long long *>(counter);
-        e = fast ? tl::launch_lane_multi_fast(a, warps, grid, smem, carveout, s)
-                 : tl::launch_lane_multi_ref(a, warps, grid, smem, carveout, s);
+        e = fast ? tl::launch_lane_multi_fast(a, warps, grid, smem, carveout, o.reg_cap, s)
+                 : tl::launch_lane_multi_ref(a, warps, grid, smem, carveout, o.reg_cap, s);
     }
     // the table copy is from pageable host memory, so the copy has been staged
     // before cudaMemcpyAsync returned and `table` may go out of scope

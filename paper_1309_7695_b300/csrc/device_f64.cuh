@@ -679,7 +679,10 @@ static __host__ __device__ __noinline__ long long ptrs_floor64(double lam, doubl
     return floor_to_ll((c.two_a / us + c.b) * U + lam + 0.43);
 }
 
-TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+// `work` (optional): [0] += iterations, [1] += acceptance tests after the
+// squeeze (the log-pmf comparison), for the launch's work counters.
+TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j,
+                          unsigned *work = nullptr)
 {
     // FP64 constants, formed on first need
     bool set64 = false;
@@ -697,6 +700,7 @@ TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t atte
         Llo = f64_to_f32(L - f32_to_f64(Lhi));
     }
     for (uint32_t it = 0; it < (uint32_t)kPtrsMaxIters; ++it) {
+        if (work) work[0] += 1;
         const uint4 w = draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
         const unsigned long long n = 2 * (((((uint64_t)w.x) << 32) | (uint64_t)w.y) >> 12) + 1;   // u = n 2^-53
         const long long dU = (long long)n - (1ll << 52);                                        // U = dU 2^-53
@@ -744,6 +748,7 @@ TL_HD long long ptrs_draw(double lam, uint64_t seed, uint32_t sim, uint32_t atte
         if (acc == 1) return (k > kCountLimit) ? kCountLimit + 1 : k;
         if (squeeze_rej || k < 0) continue;
         if (k > kCountLimit) return kCountLimit + 1;
+        if (work) work[1] += 1;
         const int sure = f32 ? ptrs_accept_certain_f(lf, k, f64_to_f32(V), f64_to_f32(us), af, bf, 2e-5f)
                              : (set64 ? ptrs_accept_certain(lam, k, V, us, c.a, c.b) : 0);
         if (sure > 0) return k;

@@ -49,7 +49,9 @@ using f64::log_pmf_f32;
 // integer, the squeeze and the acceptance test (through log_pmf) all in
 // FP32, one stream block per iteration, on the leading 23 bits of the
 // reference mode's words.
-__device__ __forceinline__ long long ptrs(float lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+// `work` (optional): [0] += iterations, [1] += acceptance tests after the squeeze.
+__device__ __forceinline__ long long ptrs(float lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j,
+                                          unsigned *work = nullptr)
 {
     const float slam = sqrtf(lam);
     const float b = 0.931f + 2.53f * slam;
@@ -57,6 +59,7 @@ __device__ __forceinline__ long long ptrs(float lam, uint64_t seed, uint32_t sim
     const float vr = 0.9277f - __fdividef(3.6224f, b - 2.0f);
     const float inv_alpha = 1.1239f + __fdividef(1.1328f, b - 3.4f);
     for (uint32_t it = 0; it < (uint32_t)f64::kPtrsMaxIters; ++it) {
+        if (work) work[0] += 1;
         const uint4 w = f64::draw(seed, sim, attempt, PURPOSE_POISSON, j, it);
         const float U = u23(w.x) - 0.5f;
         const float V = u23(w.z);
@@ -64,6 +67,7 @@ __device__ __forceinline__ long long ptrs(float lam, uint64_t seed, uint32_t sim
         const float kf = floorf((__fdividef(2.0f * a, us) + b) * U + lam + 0.43f);
         if (us >= 0.07f && V <= vr) return (long long)__float2int_rz(kf);   // kf >= 0 here for lam >= 10
         if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+        if (work) work[1] += 1;
         const float lhs = __logf(V * inv_alpha / (a / (us * us) + b));
         if (lhs <= log_pmf_f32(kf, lam)) return (long long)__float2int_rz(kf);
     }

@@ -24,9 +24,13 @@ namespace tl {
 //                  critical test: sp_a | n_a << 14 | sp_b << 16 | n_b << 30,
 //                  n = |nu| in {1, 2}, 0 for an absent entry (a reaction of
 //                  order <= 2 consumes at most two species)
+//   dmask [M]      slots (k mod 32) of the reactions k whose propensity
+//                  changes when reaction j fires (they read a species j
+//                  changes): the dirty slots of an SSA step
 struct ModelLayout {
     int32_t N, M, nnz, ndep;
-    int32_t off_rinfo, off_nu_ptr, off_nu_ent, off_tr_ptr, off_tr_ent, off_hor, off_dep_ptr, off_dep_ent, off_cinfo;
+    int32_t off_rinfo, off_nu_ptr, off_nu_ent, off_tr_ptr, off_tr_ent, off_hor, off_dep_ptr, off_dep_ent, off_cinfo,
+        off_dmask;
     int32_t words;
     int32_t max_nu_len;
 };
@@ -87,10 +91,18 @@ struct SimArgs {
     int32_t *samples;
     ssa_sim_stats *stats;
     unsigned long long *work_counter;
+    // optional per-launch work counters (SSA_WORK_* indices), added to
+    unsigned long long *work;
     // sweep moments (single-network lane launches): when non-null, every
     // recorded count x of cell (k, i) adds x, (x^2 mod 2^32) and (x^2 >> 32)
     // to moments[(k*N + i)*3 + 0..2]; samples may then be null
     unsigned long long *moments;
+    // sweep histograms (single-network lane launches): when non-null, every
+    // recorded count x of cell (k, i) adds 1 to hist[(k*N + i)*(hist_bins+2) + b],
+    // b = 0 for x < hist_lo, 1 + (x - hist_lo) / hist_width up to hist_bins, and
+    // hist_bins + 1 above; samples may then be null
+    unsigned long long *hist;
+    int32_t hist_lo, hist_width, hist_bins;
 };
 
 // Shared-memory bytes of one warp's simulation workspace.
@@ -116,19 +128,20 @@ __host__ __device__ inline size_t model_smem_bytes(const ModelLayout &L)
 // Lane-per-simulation FP64 reference kernel (kernel_lane_f64.cu): SSA steps
 // one simulation per lane, leaps and step-size selection warp-cooperative.
 size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps);
-// `carveout`: shared-memory carve-out in percent for this launch, -1 = the driver's default.
-cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
-int lane_ref_occupancy(int block_warps, size_t smem);
+// `carveout`: shared-memory carve-out in percent for this launch, -1 = the driver's default;
+// `reg_cap`: 1 selects the kernel build limited to 168 registers (three 4-warp CTAs per SM).
+cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s);
+int lane_ref_occupancy(int block_warps, size_t smem, int reg_cap);
 // Fast-mode instantiation (kernel_lane_fast.cu), same shared-memory layout.
-cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
-int lane_fast_occupancy(int block_warps, size_t smem);
+cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s);
+int lane_fast_occupancy(int block_warps, size_t smem, int reg_cap);
 // Multi-network persistent instantiations (model read from global memory;
 // workspace sized for the largest network, no model staged in shared memory).
 size_t lane_multi_smem_bytes(int max_N, int max_M, int block_warps);
-cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
-int lane_multi_ref_occupancy(int block_warps, size_t smem);
-cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s);
-int lane_multi_fast_occupancy(int block_warps, size_t smem);
+cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s);
+int lane_multi_ref_occupancy(int block_warps, size_t smem, int reg_cap);
+cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s);
+int lane_multi_fast_occupancy(int block_warps, size_t smem, int reg_cap);
 
 // ssa_simulate_multi_dev with optional per-group completion signals
 // (abi.cu): group g counts its finished simulations in done_counts[g]

@@ -34,9 +34,9 @@ struct RefArith {
         return f64::inversion_draw(lam, f64::inversion_uniform(seed, sim, attempt, j), inv);
     }
     __device__ static __forceinline__ long long ptrs(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
-                                                     uint32_t j)
+                                                     uint32_t j, unsigned *work)
     {
-        return f64::ptrs_draw(lam, seed, sim, attempt, j);
+        return f64::ptrs_draw(lam, seed, sim, attempt, j, work);
     }
 };
 
@@ -44,23 +44,23 @@ struct RefArith {
 
 size_t lane_f64_smem_bytes(const ModelLayout &L, int block_warps) { return lane_smem_bytes(L, block_warps); }
 
-cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
+cudaError_t launch_lane_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s)
 {
-    return launch_lane_impl<RefArith, false>(a, block_warps, grid, smem, carveout, s);
+    return launch_lane_impl<RefArith, false>(a, block_warps, grid, smem, carveout, reg_cap, s);
 }
 
-int lane_ref_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<RefArith, false>(block_warps, smem); }
+int lane_ref_occupancy(int block_warps, size_t smem, int reg_cap) { return lane_occupancy_impl<RefArith, false>(block_warps, smem, reg_cap); }
 
 size_t lane_multi_smem_bytes(int max_N, int max_M, int block_warps) { return lane_multi_bytes(max_N, max_M, block_warps); }
 
-cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
+cudaError_t launch_lane_multi_ref(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s)
 {
-    return launch_lane_impl<RefArith, true>(a, block_warps, grid, smem, carveout, s);
+    return launch_lane_impl<RefArith, true>(a, block_warps, grid, smem, carveout, reg_cap, s);
 }
 
-int lane_multi_ref_occupancy(int block_warps, size_t smem)
+int lane_multi_ref_occupancy(int block_warps, size_t smem, int reg_cap)
 {
-    return lane_occupancy_impl<RefArith, true>(block_warps, smem);
+    return lane_occupancy_impl<RefArith, true>(block_warps, smem, reg_cap);
 }
 
 }  // namespace tl

@@ -61,30 +61,31 @@ struct FastArith {
         return fast::inversion(f64::f64_to_f32(lam), seed, sim, attempt, j);
     }
     __device__ static __forceinline__ long long ptrs(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
-                                                     uint32_t j)
+                                                     uint32_t j, unsigned *work)
     {
-        if (f64::nn_gt((double)fast::kPtrsF32Limit, lam)) return fast::ptrs(f64::f64_to_f32(lam), seed, sim, attempt, j);
-        return f64::ptrs_draw(lam, seed, sim, attempt, j);
+        if (f64::nn_gt((double)fast::kPtrsF32Limit, lam))
+            return fast::ptrs(f64::f64_to_f32(lam), seed, sim, attempt, j, work);
+        return f64::ptrs_draw(lam, seed, sim, attempt, j, work);
     }
 };
 
 }  // namespace
 
-cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
+cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s)
 {
-    return launch_lane_impl<FastArith, false>(a, block_warps, grid, smem, carveout, s);
+    return launch_lane_impl<FastArith, false>(a, block_warps, grid, smem, carveout, reg_cap, s);
 }
 
-int lane_fast_occupancy(int block_warps, size_t smem) { return lane_occupancy_impl<FastArith, false>(block_warps, smem); }
+int lane_fast_occupancy(int block_warps, size_t smem, int reg_cap) { return lane_occupancy_impl<FastArith, false>(block_warps, smem, reg_cap); }
 
-cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
+cudaError_t launch_lane_multi_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s)
 {
-    return launch_lane_impl<FastArith, true>(a, block_warps, grid, smem, carveout, s);
+    return launch_lane_impl<FastArith, true>(a, block_warps, grid, smem, carveout, reg_cap, s);
 }
 
-int lane_multi_fast_occupancy(int block_warps, size_t smem)
+int lane_multi_fast_occupancy(int block_warps, size_t smem, int reg_cap)
 {
-    return lane_occupancy_impl<FastArith, true>(block_warps, smem);
+    return lane_occupancy_impl<FastArith, true>(block_warps, smem, reg_cap);
 }
 
 }  // namespace tl

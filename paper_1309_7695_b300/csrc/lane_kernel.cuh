@@ -40,7 +40,8 @@
 //   inv_certain(lam, stream)        k of the inversion draw when decided
 //                                   cheaply, else -1 (then inversion())
 //   inversion(lam, stream, inv)     k ~ Poisson(lam) for 0 < lam < 10
-//   ptrs(lam, stream)               k ~ Poisson(lam) for lam >= 10
+//   ptrs(lam, stream, work)         k ~ Poisson(lam) for lam >= 10 (work: optional
+//                                   iteration / acceptance-test counts)
 // Everything else -- the slot tree and its order, the critical set, tau',
 // the control flow and counters -- is shared and runs in FP64, except that
 // decisions whose FP64 operands only feed a comparison (the SSA-fallback
@@ -118,7 +119,7 @@ constexpr double kDblMax = 1.7976931348623157e308;
 
 // Everything one simulation group needs: network arrays and run arguments.
 struct GroupView {
-    const int *rinfo, *nu_ptr, *nu_ent, *tr_ptr, *tr_ent, *hor, *dep_ptr, *dep_ent, *cinfo;
+    const int *rinfo, *nu_ptr, *nu_ent, *tr_ptr, *tr_ent, *hor, *dep_ptr, *dep_ent, *cinfo, *dmask;
     int N, M, S;
     double t_end;
     const double *params;
@@ -127,6 +128,8 @@ struct GroupView {
     int32_t *samples;
     ssa_sim_stats *stats;
     unsigned long long *moments;
+    unsigned long long *hist;
+    int hist_lo, hist_width, hist_bins;
     long long sim_offset, n_sims, first;
     uint64_t seed;
     unsigned long long *done_count;
@@ -135,10 +138,16 @@ struct GroupView {
 
 // One recorded count of simulation `row`, sample k, species i: stored in the
 // trajectory array and/or added to the sweep moments of cell (k, i) (exact
-// integer sums: x, and x^2 split at bit 32 so neither word can overflow).
+// integer sums: x, and x^2 split at bit 32 so neither word can overflow)
+// and/or counted in the cell's histogram bin.
 __device__ __forceinline__ void record_count(const GroupView &G, long long row, int k, int i, int x)
 {
     if (G.samples) G.samples[((size_t)row * G.S + k) * (size_t)G.N + i] = x;
+    if (G.hist) {
+        const long long d = (long long)x - G.hist_lo;
+        const long long b = d < 0 ? 0 : min(d / G.hist_width + 1, (long long)G.hist_bins + 1);
+        atomicAdd(G.hist + ((size_t)k * G.N + i) * (size_t)(G.hist_bins + 2) + (size_t)b, 1ull);
+    }
     if (G.moments) {
         unsigned long long *c = G.moments + ((size_t)k * G.N + i) * 3;
         const unsigned long long ux = (unsigned)x, sq = ux * ux;
@@ -159,6 +168,7 @@ __device__ __forceinline__ void view_model(GroupView &G, const int *blob, const 
     G.dep_ptr = blob + L.off_dep_ptr;
     G.dep_ent = blob + L.off_dep_ent;
     G.cinfo = blob + L.off_cinfo;
+    G.dmask = blob + L.off_dmask;
     G.N = L.N;
     G.M = L.M;
 }
@@ -176,6 +186,10 @@ __device__ __forceinline__ GroupView view_single(const SimArgs &A, const int *sm
     G.samples = A.samples;
     G.stats = A.stats;
     G.moments = A.moments;
+    G.hist = A.hist;
+    G.hist_lo = A.hist_lo;
+    G.hist_width = A.hist_width;
+    G.hist_bins = A.hist_bins;
     G.sim_offset = A.sim_offset;
     G.n_sims = A.n_sims;
     G.first = 0;
@@ -199,6 +213,8 @@ __device__ __forceinline__ GroupView view_group(const GroupArgs *groups, int g)
     G.samples = R.samples;
     G.stats = R.stats;
     G.moments = nullptr;
+    G.hist = nullptr;
+    G.hist_lo = G.hist_width = G.hist_bins = 0;
     G.sim_offset = R.sim_offset;
     G.n_sims = R.n_sims;
     G.first = R.first;
@@ -208,8 +224,12 @@ __device__ __forceinline__ GroupView view_group(const GroupArgs *groups, int g)
     return G;
 }
 
-template <class Arith, bool kMulti>
-__global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
+// kRegCap = 0: up to 255 registers per thread (8-warp CTAs allowed);
+// kRegCap = 1: compiled for three 4-warp CTAs per SM (at most 168 registers),
+// the register budget a launch can choose when shared memory allows the
+// extra CTA.  Both compute the same values.
+template <class Arith, bool kMulti, int kRegCap>
+__global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_kernel(const SimArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -410,6 +430,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         // floor(x_i / |nu_ij|), read from the packed consumed-species word
                         const int *cinfo = GL.cinfo;
                         bool any_crit = false;
+                        int n_crit = 0;   // this lane's critical reactions (work counters only)
                         for (int j = lane; j < M; j += 32) {
                             const unsigned ci = (unsigned)cinfo[j];
                             const unsigned na = (ci >> 14) & 3u, nb = ci >> 30;
@@ -422,6 +443,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             const bool cr = f64::nn_pos(a) && (Lj < A.n_c);
                             w.crit[j] = cr;
                             any_crit |= cr;
+                            n_crit += cr;
                             // FP32 image of a noncritical positive propensity for the bounds
                             // below; NaN marks a value outside the range they are proved for
                             float af = 0.0f;
@@ -432,6 +454,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             w.af[j] = af;
                         }
                         any_crit = __any_sync(kFull, any_crit);
+                        if (A.work) n_crit = __reduce_add_sync(kFull, (unsigned)n_crit);
                         for (int i = lane; i < N; i += 32) w.irs[i] = 0;
                         __syncwarp();
                         for (int j = lane; j < M; j += 32) {
@@ -455,6 +478,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         //    only those are computed in FP64 (in the canonical operations).
                         const float kNoTerm = __int_as_float(0x7fc00000);   // NaN: never a candidate
                         unsigned hmin = 0x7F800000u;                          // +inf as float bits
+                        unsigned n_terms = 0, n_species = 0;                  // work counters
                         for (int i = lane; i < N; i += 32) {
                             float2 lo = make_float2(kNoTerm, kNoTerm);
                             if (w.irs[i]) {
@@ -471,6 +495,8 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                     ++n;
                                 }
                                 if (n > 0) {
+                                    n_terms += n;
+                                    n_species += 1;
                                     const int xi = X[i * kStride + L];
                                     const float xf = (float)xi;
                                     const int h = hor[i];
@@ -506,6 +532,15 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                         }
                         hmin = __reduce_min_sync(kFull, hmin);
                         const float tau1_hi = __uint_as_float(hmin);
+                        if (A.work) {
+                            n_terms = __reduce_add_sync(kFull, n_terms);
+                            n_species = __reduce_add_sync(kFull, n_species);
+                            if (lane == 0) {
+                                atomicAdd(A.work + SSA_WORK_SELECTIONS, 1ull);
+                                atomicAdd(A.work + SSA_WORK_TAU_TERMS, (unsigned long long)n_terms);
+                                atomicAdd(A.work + SSA_WORK_TAU_SPECIES, (unsigned long long)n_species);
+                            }
+                        }
                         // the threshold ssa_factor / a0 in FP32, and whether its image is trusted
                         const int e0 = (int)(f64::dbits(a0) >> 52);
                         const bool thr_ok = ssaf_ok && (e0 >= 1023 - 100 && e0 <= 1023 + 100);
@@ -657,6 +692,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                             int krej = 0, kover = 0;
                             long long ksum = 0;
                             int n_inv = 0, n_ptrs = 0;
+                            unsigned w_inv = 0, w_inv_terms = 0;   // work counters
                             const unsigned lt = (1u << lane) - 1u;
                             for (int j0 = 0; j0 < M; j0 += 32) {
                                 const int j = j0 + lane;
@@ -675,8 +711,13 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                                 kover = 1;
                                             } else if (f64::dbits(lam) < f64::dbits(10.0)) {
                                                 const int kc = Arith::inv_certain(lam, GL.seed, sL, attL, (uint32_t)j);
-                                                if (kc >= 0) kj = kc;
-                                                else cls = 1;
+                                                w_inv += 1;
+                                                if (kc >= 0) {
+                                                    kj = kc;
+                                                    w_inv_terms += (unsigned)kc;
+                                                } else {
+                                                    cls = 1;
+                                                }
                                             } else {
                                                 cls = 2;
                                             }
@@ -700,17 +741,35 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                     Arith::inversion(__longlong_as_double(w.k[j]), GL.seed, sL, attL, (uint32_t)j, inv);
                                 w.k[j] = kj;
                                 ksum += kj;
+                                w_inv_terms += (unsigned)kj;
                             }
+                            unsigned w_ptrs[2] = {0u, 0u};   // PTRS iterations, acceptance tests
                             for (int q = lane; q < n_ptrs; q += 32) {
                                 const int j = w.jl[M + q];
                                 const double lam = __longlong_as_double(w.k[j]);
                                 const long long kj = (A.mode == SSA_MODE_CLE && f64::nn_ge(lam, f64::kCleMinMean))
                                                          ? f64::normal_leap(lam, GL.seed, sL, attL, (uint32_t)j)
-                                                         : Arith::ptrs(lam, GL.seed, sL, attL, (uint32_t)j);
+                                                         : Arith::ptrs(lam, GL.seed, sL, attL, (uint32_t)j,
+                                                                       A.work ? w_ptrs : nullptr);
                                 if (kj < 0) krej = 1;
                                 else if (kj > f64::kCountLimit) kover = 1;
                                 w.k[j] = kj;
                                 ksum += kj;
+                            }
+                            if (A.work) {
+                                w_inv = __reduce_add_sync(kFull, w_inv);
+                                w_inv_terms = __reduce_add_sync(kFull, w_inv_terms);
+                                w_ptrs[0] = __reduce_add_sync(kFull, w_ptrs[0]);
+                                w_ptrs[1] = __reduce_add_sync(kFull, w_ptrs[1]);
+                                if (lane == 0) {
+                                    if (f64::nn_pos(a0c)) atomicAdd(A.work + SSA_WORK_TAU2, 1ull);
+                                    atomicAdd(A.work + SSA_WORK_MEANS, (unsigned long long)(M - n_crit));
+                                    atomicAdd(A.work + SSA_WORK_INV_DRAWS, (unsigned long long)w_inv);
+                                    atomicAdd(A.work + SSA_WORK_INV_TERMS, (unsigned long long)w_inv_terms);
+                                    atomicAdd(A.work + SSA_WORK_PTRS_DRAWS, (unsigned long long)n_ptrs);
+                                    atomicAdd(A.work + SSA_WORK_PTRS_ITERS, (unsigned long long)w_ptrs[0]);
+                                    atomicAdd(A.work + SSA_WORK_PTRS_TESTS, (unsigned long long)w_ptrs[1]);
+                                }
                             }
                             if (__any_sync(kFull, krej)) {
                                 stL = SSA_STATUS_REJECT_LIMIT;
@@ -751,7 +810,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 break;
                             }
                             for (int i = lane; i < N; i += 32) X[i * kStride + L] = (int)w.xn[i];
-                            fiL += warp_sum_i64(ksum);
+                            fiL += warp_sum_counts(ksum);
                             tL = clamp ? t_stop : tL + tau;
                             lpL += 1;
                             break;
@@ -811,7 +870,7 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
         // ---- lane-local part: one exact SSA step (direct method)
         if (phase == P_SSA) {
             const GroupView G = gview(grp);
-            const int *nu_ptr = G.nu_ptr, *nu_ent = G.nu_ent, *dep_ptr = G.dep_ptr, *dep_ent = G.dep_ent;
+            const int *nu_ptr = G.nu_ptr, *nu_ent = G.nu_ent;
             const int M = G.M, S = G.S;
             const double *T = G.T;
             const double t_end = G.t_end;
@@ -893,18 +952,50 @@ __global__ void __launch_bounds__(256, 1) lane_kernel(const SimArgs A)
                                 status = SSA_STATUS_OVERFLOW;
                                 phase = P_DONE;
                             } else {
-                                unsigned dirty = 0;
+                                unsigned dirty = (unsigned)G.dmask[jf];
                                 for (int e = e0; e < e1; ++e) {
                                     const int ent = nu_ent[e];
-                                    const int sp = ent >> 8;
-                                    X[sp * kStride + lane] += (signed char)(ent & 0xff);
-                                    for (int d = dep_ptr[sp]; d < dep_ptr[sp + 1]; ++d) dirty |= 1u << (dep_ent[d] & 31);
+                                    X[(ent >> 8) * kStride + lane] += (signed char)(ent & 0xff);
                                 }
+                                // re-sum the dirty slots (l < M: a dirty slot holds a reaction); up
+                                // to four reactions per slot, the next slot's rate constants are
+                                // loaded while the current slot is summed
                                 unsigned m = dirty;
-                                while (m) {
-                                    const int l = __ffs(m) - 1;
+                                if (m != 0 && M <= 128) {
+                                    const double *cp = G.params + (size_t)row * M;
+                                    int l = __ffs(m) - 1;
                                     m &= m - 1;
-                                    V[l * kStride + lane] = own_slot_sum(G, l);   // l < M: a dirty slot holds a reaction
+                                    double c0 = __ldg(cp + l), c1 = (l + 32 < M) ? __ldg(cp + l + 32) : 0.0;
+                                    double c2 = (l + 64 < M) ? __ldg(cp + l + 64) : 0.0;
+                                    double c3 = (l + 96 < M) ? __ldg(cp + l + 96) : 0.0;
+                                    for (;;) {
+                                        const int ln = m ? __ffs(m) - 1 : -1;
+                                        m &= m - 1;
+                                        double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
+                                        if (ln >= 0) {
+                                            n0 = __ldg(cp + ln);
+                                            if (ln + 32 < M) n1 = __ldg(cp + ln + 32);
+                                            if (ln + 64 < M) n2 = __ldg(cp + ln + 64);
+                                            if (ln + 96 < M) n3 = __ldg(cp + ln + 96);
+                                        }
+                                        double sl = f64::first_term(Arith::prop(G.rinfo[l], c0, X, kStride, lane));
+                                        if (l + 32 < M) sl = sl + Arith::prop(G.rinfo[l + 32], c1, X, kStride, lane);
+                                        if (l + 64 < M) sl = sl + Arith::prop(G.rinfo[l + 64], c2, X, kStride, lane);
+                                        if (l + 96 < M) sl = sl + Arith::prop(G.rinfo[l + 96], c3, X, kStride, lane);
+                                        V[l * kStride + lane] = sl;
+                                        if (ln < 0) break;
+                                        l = ln;
+                                        c0 = n0;
+                                        c1 = n1;
+                                        c2 = n2;
+                                        c3 = n3;
+                                    }
+                                } else {
+                                    while (m) {
+                                        const int l = __ffs(m) - 1;
+                                        m &= m - 1;
+                                        V[l * kStride + lane] = own_slot_sum(G, l);
+                                    }
                                 }
 #pragma unroll
                                 for (int k = 1; k <= 5; ++k) {
@@ -975,33 +1066,51 @@ inline size_t lane_multi_bytes(int max_N, int max_M, int block_warps)
     return lane::r16((size_t)f64::kInvTable * 8) + (size_t)block_warps * lane::lane_warp_bytes(max_N, max_M);
 }
 
-template <class Arith, bool kMulti>
-cudaError_t launch_lane_impl(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
+template <class Arith, bool kMulti, int kRegCap>
+cudaError_t launch_lane_variant(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, cudaStream_t s)
 {
-    cudaError_t e = f64::ensure_log_table(s);
+    cudaError_t e = cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti, kRegCap>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti, kRegCap>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             carveout);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
-    if (e != cudaSuccess) return e;
-    lane::lane_kernel<Arith, kMulti><<<grid, block_warps * 32, smem, s>>>(a);
+    lane::lane_kernel<Arith, kMulti, kRegCap><<<grid, block_warps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+// reg_cap: 0 = the default build, 1 = the 168-register build (block_warps <= 4)
 template <class Arith, bool kMulti>
-int lane_occupancy_impl(int block_warps, size_t smem)
+cudaError_t launch_lane_impl(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap,
+                             cudaStream_t s)
+{
+    cudaError_t e = f64::ensure_log_table(s);
+    if (e != cudaSuccess) return e;
+    if (reg_cap) return launch_lane_variant<Arith, kMulti, 1>(a, block_warps, grid, smem, carveout, s);
+    return launch_lane_variant<Arith, kMulti, 0>(a, block_warps, grid, smem, carveout, s);
+}
+
+template <class Arith, bool kMulti, int kRegCap>
+int lane_occupancy_variant(int block_warps, size_t smem)
 {
     int nb = 0;
     // the carve-out a previous launch may have set would cap the answer: query at the default
-    if (cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti, kRegCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti>, cudaFuncAttributePreferredSharedMemoryCarveout, -1) !=
-            cudaSuccess)
+        cudaFuncSetAttribute(lane::lane_kernel<Arith, kMulti, kRegCap>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             -1) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lane::lane_kernel<Arith, kMulti>, block_warps * 32, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lane::lane_kernel<Arith, kMulti, kRegCap>, block_warps * 32,
+                                                      smem) != cudaSuccess)
         return 0;
     return nb;
+}
+
+template <class Arith, bool kMulti>
+int lane_occupancy_impl(int block_warps, size_t smem, int reg_cap)
+{
+    return reg_cap ? lane_occupancy_variant<Arith, kMulti, 1>(block_warps, smem)
+                   : lane_occupancy_variant<Arith, kMulti, 0>(block_warps, smem);
 }
 
 }  // namespace tl

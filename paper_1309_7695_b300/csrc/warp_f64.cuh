@@ -65,12 +65,22 @@ __device__ __forceinline__ double propensity(int info, double c, const int *x)
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 {
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(kFull, v, d);
-        v = o < v ? o : v;
-    }
-    return v;
+    // the minimum of the high words, then the minimum low word among the
+    // lanes that hold it (two hardware reductions instead of five shuffle
+    // rounds of 64-bit values)
+    const unsigned hi = __reduce_min_sync(kFull, (unsigned)(v >> 32));
+    const unsigned lo = __reduce_min_sync(kFull, (unsigned)(v >> 32) == hi ? (unsigned)v : 0xFFFFFFFFu);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Sum over the warp of 0 <= v < 2^50 (a lane's Poisson counts of one leap:
+// at most 2^14 reactions per lane, each at most 2^40 + 1): the low 24 and the
+// high 26 bits are summed by two 32-bit hardware reductions without overflow.
+__device__ __forceinline__ long long warp_sum_counts(long long v)
+{
+    const unsigned lo = __reduce_add_sync(kFull, (unsigned)(v & 0xFFFFFF));
+    const unsigned hi = __reduce_add_sync(kFull, (unsigned)(v >> 24));
+    return ((long long)hi << 24) + (long long)lo;
 }
 
 __device__ __forceinline__ long long warp_sum_i64(long long v)
