@@ -164,7 +164,7 @@ def config_dict(extra=None):
     return d
 
 
-def cpu_oracle_rate(batch, n_sample=2048, seed=1000):
+def cpu_oracle_rate(batch, n_sample=2048, seed=1000, gpu_stats=None):
     """Oracle firings/s and sim-steps/s on an evenly strided sample of the
     batch (every (n/n_sample)-th simulation, so heavy and light simulations
     appear in their batch proportions), all host cores, OpenMP over
@@ -186,6 +186,21 @@ def cpu_oracle_rate(batch, n_sample=2048, seed=1000):
         return float(st["firings"].sum()) / dt, float(st["leaps"].sum() + st["ssa_steps"].sum()) / dt, dt
 
     fir, steps, dt = timed(rows, cores)
+    mix = None
+    heavy = None
+    if gpu_stats is not None:
+        # the sample's work mix against the batch's (the GPU ran the same batch and seed), and the
+        # oracle's rate on the batch's heaviest simulations, which set the length of a GPU launch
+        capped = gpu_stats["status"] == 1
+        att = gpu_stats["attempts"].astype(np.float64)
+        mix = {"sample_capped": int(capped[rows].sum()), "batch_capped": int(capped.sum()),
+               "batch_attempt_share_of_capped": float(att[capped].sum() / att.sum()),
+               "sample_attempt_share_of_batch": float(att[rows].sum() / att.sum())}
+        top = np.argsort(-att)[:4]
+        hf, hs, hd = timed(np.sort(top), min(cores, 4))
+        heavy = {"value": hf, "unit": "firings/s", "sim_steps_per_s": hs, "seconds": round(hd, 2),
+                 "threads": min(cores, 4), "sample": "the 4 simulations of the batch with the most attempts "
+                                                     "(one thread each)"}
     rows1 = rows[::8]
     f1, s1, d1 = timed(rows1, 1)
     fa, sa, da = timed(rows1, cores)   # the same simulations on all cores (restores the thread count)
@@ -195,7 +210,8 @@ def cpu_oracle_rate(batch, n_sample=2048, seed=1000):
     return {"value": fir, "unit": "firings/s", "sim_steps_per_s": steps,
             "cores": cores, "kind": "oracle", "seconds": round(dt, 2),
             "sample": f"every {stride}th of the {batch.n_sims} simulations ({len(rows)} simulations, "
-                      f"seed {seed}), OpenMP over simulations", "one_core": one_core}
+                      f"seed {seed}), OpenMP over simulations", "one_core": one_core, "mix": mix,
+            "heaviest": heavy}
 
 
 def run_reference(args):
@@ -282,13 +298,16 @@ def run_hetero(args):
     ordered, topts, costs = autotune.plan(gd, precision=abi.SSA_FAST)
     t_plan = time.perf_counter() - t0
     topts.max_attempts = cap
-    t_plain = timed(plain)
-    f_plain, s_plain = totals()
+    t_plain = f_plain = s_plain = None
+    if not args.hetero_no_plain:
+        t_plain = timed(plain)
+        f_plain, s_plain = totals()
     t_multi = timed(lambda: abi.ssa_simulate_multi_dev(ordered, opts=topts))
     f_multi, s_multi = totals()
     line = {"metric": METRIC, "workload": "hetero", "value": f_multi / t_multi, "unit": "firings/s",
-            "sim_steps_per_s": s_multi / t_multi, "plain_value": f_plain / t_plain,
-            "plain_sim_steps_per_s": s_plain / t_plain, "speedup_vs_plain": t_plain / t_multi,
+            "sim_steps_per_s": s_multi / t_multi, "plain_value": f_plain / t_plain if t_plain else None,
+            "plain_sim_steps_per_s": s_plain / t_plain if t_plain else None,
+            "speedup_vs_plain": t_plain / t_multi if t_plain else None,
             "seconds_persistent": t_multi, "seconds_plain": t_plain, "seconds_planning": t_plan,
             "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'", "data": "synthetic",
             "config": {"workload": f"heterogeneous batch: {len(gd)} groups over 8 random networks (8..512 reactions, "
@@ -565,6 +584,8 @@ def main():
     ap.add_argument("--no-fast", action="store_true")
     ap.add_argument("--no-moments", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-work-counters", action="store_true",
+                    help="skip the untimed replay that counts the method's work (the roofline is then omitted)")
     ap.add_argument("--side-batches", type=int, default=8,
                     help="batches simulated by each side leg (fast, persistent, moments, end to end)")
     ap.add_argument("--served-rate", type=float, default=0.5, help="arrival rate of the short served leg (1/s)")
@@ -578,6 +599,7 @@ def main():
     ap.add_argument("--rre-samples", type=int, default=11)
     ap.add_argument("--cle-sims", type=int, default=16384)
     ap.add_argument("--hetero-sims", type=int, default=20000)
+    ap.add_argument("--hetero-no-plain", action="store_true", help="skip the one-launch-per-network comparison")
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--serve-networks", type=int, default=32)
     ap.add_argument("--serve-cap", type=int, default=1 << 18)
@@ -704,11 +726,17 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    local_t, stats, launches = run([1000 + k for k in range(args.steps)], head_prec, args.schedule, counted=True)
+    local_t, stats, launches = run([1000 + k for k in range(args.steps)], head_prec, args.schedule)
     clk = clocks.stop()
     barrier()
     fir, simsteps = totals(stats)
-    wk = work.cpu().numpy().astype(np.float64)
+    # the algorithmic work of the timed batches: the same launches replayed, untimed, with the work
+    # counters on (the simulations are deterministic, so the replay does exactly the timed work)
+    wk = np.zeros(abi.SSA_WORK_COUNTERS)
+    if not args.no_work_counters:
+        work.zero_()
+        run([1000 + k for k in range(args.steps)], head_prec, args.schedule, counted=True)
+        wk = work.cpu().numpy().astype(np.float64)
     ops = sum(algorithmic_fp64_ops(s, wk / len(stats), net) for s in stats)
     capped = sum(int((s["status"] == abi.SSA_STATUS_STEP_LIMIT).sum()) for s in stats)
     t_max, (fir, simsteps, ops, capped) = shard.reduce_run(local_t, [fir, simsteps, ops, capped], device=dev)
@@ -734,9 +762,10 @@ def main():
                 "ms_per_step": ft * 1e3 / args.steps, "batches": args.steps, "schedule": sched_name(args.schedule),
                 "vs_fp64": (ff / ft) / (fir / t_max), "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'"}
         seeds = [1000 + k for k in range(side_k)]
-        work.zero_()
-        mt, mstats, _ = run(seeds, abi.SSA_FAST, "multi", counted=True)
+        mt, mstats, _ = run(seeds, abi.SSA_FAST, "multi")
         mf, msteps = totals(mstats)
+        work.zero_()
+        run(seeds, abi.SSA_FAST, "multi", counted=True)
         mwk = work.cpu().numpy().astype(np.float64)
         mops = sum(algorithmic_fp64_ops(s, mwk / len(mstats), net) for s in mstats)
         mt, (mf, msteps, mops) = shard.reduce_run(mt, [mf, msteps, mops], device=dev)
@@ -819,7 +848,8 @@ def main():
                                        "capped_fraction": capped / (world * n * args.steps), "schedule": sched,
                                        "l2": "each step reads 41 MB of inputs and writes 847 MB of samples (> L2); "
                                              "L2 flushed before the timed region"}),
-                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "roofline": None if args.no_work_counters else {
+                             "bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                              "unit": "T FP64-op/s", "frac": achieved / peak_ops, "traffic": None,
                              "kernel": kernel_name(args),
                              "peak_source": "of measured: FP64 add rate of this device, measured live by "
@@ -832,7 +862,7 @@ def main():
                 "clocks": clk, "gpu_launches": launches, "e2e": e2e, "plain_fp64": plain, "fast_mode": fast,
                 "fast_persistent": fast_persistent, "served": served, "moments_mode": moments}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_rate(batch)
+            line["cpu_baseline"] = cpu_oracle_rate(batch, gpu_stats=stats[0])
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

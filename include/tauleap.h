@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define SSA_ABI_VERSION 1
+#define SSA_ABI_VERSION 2
 
 /* return codes */
 #define SSA_OK 0

@@ -26,10 +26,8 @@ constexpr float kPtrsF32Limit = 0x1p22f;
 
 // Inversion by sequential search for 0 < lam < 10 with the FP32 cdf, on the
 // leading 23 bits of the reference mode's inversion uniform.
-__device__ __forceinline__ long long inversion(float lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+__device__ __forceinline__ long long inversion_u(float lam, float u)
 {
-    const uint4 w = f64::draw(seed, sim, attempt, PURPOSE_POISSON, j, 0);
-    const float u = u23(w.x);
     float p = __expf(-lam);
     float F = p;
     int k = 0;
@@ -41,6 +39,11 @@ __device__ __forceinline__ long long inversion(float lam, uint64_t seed, uint32_
         F = Fn;
     }
     return k;
+}
+__device__ __forceinline__ long long inversion(float lam, uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t j)
+{
+    const uint4 w = f64::draw(seed, sim, attempt, PURPOSE_POISSON, j, 0);
+    return inversion_u(lam, u23(w.x));
 }
 
 using f64::log_pmf_f32;

@@ -28,6 +28,17 @@ struct RefArith {
     {
         return f64::inversion_certain(lam, f64::inversion_uniform(seed, sim, attempt, j));
     }
+    // the same decisions from a Philox block already drawn: the leap's block, and
+    // block 0 of reaction j's Poisson stream
+    __device__ static __forceinline__ void uniforms_of(uint4 w, double &ua, double &ub)
+    {
+        ua = f64::u01(w.x, w.y);
+        ub = f64::u01(w.z, w.w);
+    }
+    __device__ static __forceinline__ int inv_certain_of(double lam, uint4 w)
+    {
+        return f64::inversion_certain(lam, f64::u01(w.x, w.y));
+    }
     __device__ static __forceinline__ long long inversion(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
                                                           uint32_t j, const double *inv)
     {

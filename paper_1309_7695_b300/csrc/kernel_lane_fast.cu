@@ -55,6 +55,15 @@ struct FastArith {
         // the FP32 inversion is the fast-mode definition: always decided here
         return (int)fast::inversion(f64::f64_to_f32(lam), seed, sim, attempt, j);
     }
+    __device__ static __forceinline__ void uniforms_of(uint4 w, double &ua, double &ub)
+    {
+        ua = f64::u01(w.x, w.y);
+        ub = f64::u01(w.z, w.w);
+    }
+    __device__ static __forceinline__ int inv_certain_of(double lam, uint4 w)
+    {
+        return (int)fast::inversion_u(f64::f64_to_f32(lam), fast::u23(w.x));
+    }
     __device__ static __forceinline__ long long inversion(double lam, uint64_t seed, uint32_t sim, uint32_t attempt,
                                                           uint32_t j, const double *)
     {

@@ -148,12 +148,14 @@ __device__ __forceinline__ void record_count(const GroupView &G, long long row, 
         const long long b = d < 0 ? 0 : min(d / G.hist_width + 1, (long long)G.hist_bins + 1);
         atomicAdd(G.hist + ((size_t)k * G.N + i) * (size_t)(G.hist_bins + 2) + (size_t)b, 1ull);
     }
-    if (G.moments) {
+    if (G.moments && x != 0) {
+        // adding zero changes no sum: a zero count adds nothing, and a count
+        // below 2^16 has no high square word
         unsigned long long *c = G.moments + ((size_t)k * G.N + i) * 3;
         const unsigned long long ux = (unsigned)x, sq = ux * ux;
         atomicAdd(c, ux);
         atomicAdd(c + 1, sq & 0xFFFFFFFFull);
-        atomicAdd(c + 2, sq >> 32);
+        if (sq >> 32) atomicAdd(c + 2, sq >> 32);
     }
 }
 
@@ -402,17 +404,58 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                     stL = SSA_STATUS_STEP_LIMIT;
                     nphase = P_DONE;
                 } else {
-                    double s = 0.0;
-                    if (lane < M) {   // first term of the slot sum (no add to +0)
-                        const double a = Arith::prop(rinfo[lane], w.c[lane], X, kStride, L);
-                        w.a[lane] = a;
-                        s = f64::first_term(a);
-                    }
-                    for (int j = lane + 32; j < M; j += 32) {
-                        const double a = Arith::prop(rinfo[j], w.c[j], X, kStride, L);
+                    // The Philox blocks of this visit's first leap attempt depend only on
+                    // (simulation, attempt, reaction): drawn here, the three independent
+                    // chains (the leap's block and block 0 of the Poisson streams of this
+                    // lane's first two reactions) run together, off the leap's path.
+                    const uint32_t att1 = attL + 1;
+                    const uint4 w_leap1 = f64::draw(GL.seed, sL, att1, PURPOSE_LEAP, 0, 0);
+                    const uint4 w_pois1a = f64::draw(GL.seed, sL, att1, PURPOSE_POISSON, (uint32_t)lane, 0);
+                    const uint4 w_pois1b = f64::draw(GL.seed, sL, att1, PURPOSE_POISSON, (uint32_t)(lane + 32), 0);
+                    // One pass over this lane's reactions j = lane, lane + 32, ...: the
+                    // propensity and its slot sum, the critical test (CGP 2005: L_j = min
+                    // over the species j consumes of floor(x_i / |nu_ij|), from the packed
+                    // consumed-species word), the FP32 image of a noncritical positive
+                    // propensity for the tau' bounds (NaN outside the range they are
+                    // proved for), and the reactant species of the noncritical reactions
+                    // (I_rs).  The results are used only when a0 turns out positive.
+                    const int *cinfo = GL.cinfo;
+                    for (int i = lane; i < N; i += 32) w.irs[i] = 0;
+                    __syncwarp();
+                    bool any_crit = false;
+                    int n_crit = 0;   // this lane's critical reactions (work counters only)
+                    auto reaction = [&](int j) -> double {
+                        const int info = rinfo[j];
+                        const double a = Arith::prop(info, w.c[j], X, kStride, L);
                         w.a[j] = a;
-                        s = s + a;
-                    }
+                        const unsigned ci = (unsigned)cinfo[j];
+                        const unsigned na = (ci >> 14) & 3u, nb = ci >> 30;
+                        const int xa = X[(ci & 0x3fffu) * kStride + L];
+                        const int xb = X[((ci >> 16) & 0x3fffu) * kStride + L];
+                        int Lj = INT_MAX;
+                        if (na) Lj = (na == 1) ? xa : (xa >> 1);
+                        if (nb) Lj = min(Lj, (nb == 1) ? xb : (xb >> 1));
+                        const bool cr = f64::nn_pos(a) && (Lj < A.n_c);
+                        w.crit[j] = cr;
+                        any_crit |= cr;
+                        n_crit += cr;
+                        float af = 0.0f;
+                        if (!cr) {
+                            if (f64::nn_pos(a)) {
+                                const int ea = (int)(f64::dbits(a) >> 52);
+                                af = (ea >= 1023 - 100 && ea <= 1023 + 100) ? f64::f64_to_f32(a)
+                                                                           : __int_as_float(0x7fc00000);
+                            }
+                            const int kind = info & 3;
+                            if (kind >= 1) w.irs[(info >> 2) & 0x7fff] = 1;
+                            if (kind == 2) w.irs[(info >> 17) & 0x7fff] = 1;
+                        }
+                        w.af[j] = af;
+                        return a;
+                    };
+                    double s = 0.0;
+                    if (lane < M) s = f64::first_term(reaction(lane));   // first term of the slot sum (no add to +0)
+                    for (int j = lane + 32; j < M; j += 32) s = s + reaction(j);
                     double Lv[6];
                     const double a0 = slot_tree(s, Lv);
 #pragma unroll
@@ -426,45 +469,8 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                         stL = SSA_STATUS_INVALID;
                         nphase = P_DONE;
                     } else {
-                        // critical set (CGP 2005): L_j = min over the species j consumes of
-                        // floor(x_i / |nu_ij|), read from the packed consumed-species word
-                        const int *cinfo = GL.cinfo;
-                        bool any_crit = false;
-                        int n_crit = 0;   // this lane's critical reactions (work counters only)
-                        for (int j = lane; j < M; j += 32) {
-                            const unsigned ci = (unsigned)cinfo[j];
-                            const unsigned na = (ci >> 14) & 3u, nb = ci >> 30;
-                            const int xa = X[(ci & 0x3fffu) * kStride + L];
-                            const int xb = X[((ci >> 16) & 0x3fffu) * kStride + L];
-                            int Lj = INT_MAX;
-                            if (na) Lj = (na == 1) ? xa : (xa >> 1);
-                            if (nb) Lj = min(Lj, (nb == 1) ? xb : (xb >> 1));
-                            const double a = w.a[j];
-                            const bool cr = f64::nn_pos(a) && (Lj < A.n_c);
-                            w.crit[j] = cr;
-                            any_crit |= cr;
-                            n_crit += cr;
-                            // FP32 image of a noncritical positive propensity for the bounds
-                            // below; NaN marks a value outside the range they are proved for
-                            float af = 0.0f;
-                            if (!cr && f64::nn_pos(a)) {
-                                const int ea = (int)(f64::dbits(a) >> 52);
-                                af = (ea >= 1023 - 100 && ea <= 1023 + 100) ? f64::f64_to_f32(a) : __int_as_float(0x7fc00000);
-                            }
-                            w.af[j] = af;
-                        }
                         any_crit = __any_sync(kFull, any_crit);
                         if (A.work) n_crit = __reduce_add_sync(kFull, (unsigned)n_crit);
-                        for (int i = lane; i < N; i += 32) w.irs[i] = 0;
-                        __syncwarp();
-                        for (int j = lane; j < M; j += 32) {
-                            if (w.crit[j]) continue;
-                            const int info = rinfo[j];
-                            const int kind = info & 3;
-                            if (kind >= 1) w.irs[(info >> 2) & 0x7fff] = 1;
-                            if (kind == 2) w.irs[(info >> 17) & 0x7fff] = 1;
-                        }
-                        __syncwarp();
                         // Certified FP32 bounds on every tau' term (CGP 2006).  mu and sigma^2
                         // summed in FP32 from the FP32 images of the a_j are within
                         // (n + 4) 2^-20 of the sum of |nu a| of the exact sums (n terms), and
@@ -656,7 +662,8 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                             }
                             attL = attL + 1;
                             double u_tau, u_sel;
-                            Arith::uniforms(GL.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
+                            if (attL == att1) Arith::uniforms_of(w_leap1, u_tau, u_sel);
+                            else Arith::uniforms(GL.seed, sL, attL, PURPOSE_LEAP, u_tau, u_sel);
                             const double t_stop = (ksL < S) ? tnL : t_end;
                             const double delta = t_stop - tL;
                             // tau'' matters only if it can be the smallest of tau'', tau' and
@@ -710,7 +717,10 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                                                 kj = f64::kCountLimit + 1;
                                                 kover = 1;
                                             } else if (f64::dbits(lam) < f64::dbits(10.0)) {
-                                                const int kc = Arith::inv_certain(lam, GL.seed, sL, attL, (uint32_t)j);
+                                                const int kc =
+                                                    (attL == att1 && j0 < 64)
+                                                        ? Arith::inv_certain_of(lam, j0 == 0 ? w_pois1a : w_pois1b)
+                                                        : Arith::inv_certain(lam, GL.seed, sL, attL, (uint32_t)j);
                                                 w_inv += 1;
                                                 if (kc >= 0) {
                                                     kj = kc;

@@ -50,7 +50,7 @@ def test_host_side_validation_without_gpu(libpath):
     # model validation runs on the host before any CUDA call
     from paper_1309_7695_b300 import abi, inputs
     lib = abi.lib()
-    assert lib.ssa_abi_version() == 1
+    assert lib.ssa_abi_version() == 2
     o = abi.ssa_default_options()
     assert o.eps == 0.03 and o.n_c == 10 and o.ssa_block == 100 and o.max_attempts == 10**8
     bad = inputs.Network(2, [[(0, 2), (1, 1)]], [[]])     # order 3

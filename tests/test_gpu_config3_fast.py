@@ -36,7 +36,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 from paper_1309_7695_b300 import abi  # noqa: E402
-from test_gpu_fast_mode import holm_reject, moment_and_ks_report, run  # noqa: E402
+from test_gpu_fast_mode import moment_and_ks_report, run  # noqa: E402
 
 N, M, T_END = 128, 256, 100.0
 CAP = 1 << 22

@@ -46,14 +46,16 @@ def fetch(g):
     return g["samples"].cpu().numpy(), g["stats"].cpu().numpy().view(abi.STATS_DTYPE).reshape(n)
 
 
-@pytest.mark.parametrize("order", [[0, 1, 2, 3, 4], [4, 2, 0, 3, 1]], ids=["given", "shuffled"])
+@pytest.mark.parametrize("order,reg_cap", [([0, 1, 2, 3, 4], 0), ([4, 2, 0, 3, 1], 0), ([4, 2, 0, 3, 1], 1)],
+                         ids=["given", "shuffled", "shuffled-168reg"])
 @pytest.mark.parametrize("mode", [abi.SSA_MODE_TAU_LEAP, abi.SSA_MODE_EXACT], ids=["tau", "exact"])
-def test_multi_equals_single_and_oracle(order, mode):
+def test_multi_equals_single_and_oracle(order, reg_cap, mode):
     fx = groups_fixture()
     models = [abi.Model(b.network) for b, _ in fx]
     opts = abi.ssa_default_options(mode=mode, max_attempts=CAP)
     multi = [to_dev(b, m, seed) for (b, seed), m in zip(fx, models)]
-    abi.ssa_simulate_multi_dev([multi[k] for k in order], opts=opts)
+    abi.ssa_simulate_multi_dev([multi[k] for k in order], opts=abi.ssa_default_options(mode=mode, max_attempts=CAP,
+                                                                                          reg_cap=reg_cap))
     torch.cuda.synchronize()
     for (b, seed), m, g in zip(fx, models, multi):
         single = to_dev(b, m, seed)

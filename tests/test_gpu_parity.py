@@ -150,13 +150,21 @@ def test_degenerate_sizes(layout):
     assert_same(gpu_run(one, layout=layout), oracle_run(one), "n=1")
 
 
-@pytest.mark.parametrize("block_warps,sims_per_warp", [(1, 0), (2, 0), (4, 0), (8, 0), (4, 1), (2, 7), (1, 16)])
-def test_launch_shape_does_not_change_results(block_warps, sims_per_warp):
+@pytest.mark.parametrize("block_warps,sims_per_warp,ctas_per_sm,reg_cap",
+                         [(1, 0, 0, 0), (2, 0, 0, 0), (4, 0, 0, 0), (8, 0, 0, 0), (4, 1, 0, 0), (2, 7, 0, 0),
+                          (1, 16, 0, 0), (4, 0, 1, 0), (4, 0, 0, 1), (2, 16, 0, 1), (4, 0, 1, 1)])
+def test_launch_shape_does_not_change_results(block_warps, sims_per_warp, ctas_per_sm, reg_cap):
+    # the register-budget build and the carve-out for fewer CTAs per SM included
     b = inputs.random_batch(32, 64, 300, seed=12, t_end=20.0, n_samples=11)
     ref = gpu_run(b, seed=3, max_attempts=100_000, layout=abi.SSA_LAYOUT_WARP)
     got = gpu_run(b, seed=3, max_attempts=100_000, layout=abi.SSA_LAYOUT_LANE, block_warps=block_warps,
-                  sims_per_warp=sims_per_warp)
-    assert_same(got, ref, f"block_warps={block_warps} sims_per_warp={sims_per_warp}")
+                  sims_per_warp=sims_per_warp, ctas_per_sm=ctas_per_sm, reg_cap=reg_cap)
+    assert_same(got, ref, f"block_warps={block_warps} sims_per_warp={sims_per_warp} ctas={ctas_per_sm} reg={reg_cap}")
+    if reg_cap == 0 and ctas_per_sm == 0 and block_warps == 4:
+        # the 168-register build of fast mode gives the fast-mode results of the default build
+        f0 = gpu_run(b, seed=3, max_attempts=100_000, precision=abi.SSA_FAST)
+        f1 = gpu_run(b, seed=3, max_attempts=100_000, precision=abi.SSA_FAST, reg_cap=1)
+        assert_same(f1, f0, "fast reg_cap")
 
 
 def test_sharding_by_sim_offset_is_bit_identical():
