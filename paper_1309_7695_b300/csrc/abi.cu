@@ -393,10 +393,20 @@ int simulate_dev_impl(ssa_model_t m, int64_t n_sims, int64_t sim_offset, const d
     if (!counter_in) TL_CUDA(cudaMallocAsync(&counter, sizeof(unsigned long long), s));
     a.work_counter = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    // fast mode: the rate constants' FP32 images, formed once for the launch (the
+    // allocation-free path, which has no place for them, converts them on use instead)
+    void *params_f = nullptr;
+    const long long n_par = n_sims * (long long)m->L.M;
+    if (e == cudaSuccess && fast && layout == SSA_LAYOUT_LANE && !counter_in) {
+        e = cudaMallocAsync(&params_f, sizeof(float) * (size_t)n_par, s);
+        if (e == cudaSuccess) e = tl::launch_params_to_f32(params, static_cast<float *>(params_f), n_par, s);
+        a.params_f = static_cast<const float *>(params_f);
+    }
     if (e == cudaSuccess)
         e = layout == SSA_LAYOUT_LANE ? (fast ? tl::launch_lane_fast(a, warps, grid, smem, carveout, rc_var, s)
                                               : tl::launch_lane_ref(a, warps, grid, smem, carveout, rc_var, s))
                                       : tl::launch_warp_ref(a, warps, grid, smem, s);
+    if (params_f) cudaFreeAsync(params_f, s);
     cudaError_t e2 = counter_in ? cudaSuccess : cudaFreeAsync(counter, s);
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(SSA_ECUDA, std::string("cudaFreeAsync: ") + cudaGetErrorString(e2));
@@ -778,10 +788,35 @@ int simulate_multi_impl(int32_t n_groups, const ssa_group *groups, const ssa_opt
     a.max_attempts = o.max_attempts;
     a.sims_per_warp = spw;
     a.work = reinterpret_cast<unsigned long long *>(o.work_counters);
-    void *d_table = nullptr, *counter = nullptr;
+    void *d_table = nullptr, *counter = nullptr, *params_f = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (fast) {
+        // the rate constants' FP32 images, formed once for the launch
+        long long total = 0;
+        for (const auto &R : table) total += R.n_sims * (long long)R.L.M;
+        if (total > 0) e = cudaMallocAsync(&params_f, sizeof(float) * (size_t)total, s);
+        long long off = 0;
+        for (auto &R : table) {
+            const long long cnt = R.n_sims * (long long)R.L.M;
+            if (e == cudaSuccess && cnt > 0) {
+                float *dst = static_cast<float *>(params_f) + off;
+                e = tl::launch_params_to_f32(R.params, dst, cnt, s);
+                R.params_f = dst;
+            }
+            off += cnt;
+        }
+        if (e != cudaSuccess) {
+            if (params_f) cudaFreeAsync(params_f, s);
+            return fail(SSA_ECUDA, std::string("rate constants to FP32: ") + cudaGetErrorString(e));
+        }
+    }
     const size_t table_bytes = sizeof(tl::GroupArgs) * table.size();
-    TL_CUDA(cudaMallocAsync(&d_table, table_bytes, s));
-    cudaError_t e = cudaMemcpyAsync(d_table, table.data(), table_bytes, cudaMemcpyHostToDevice, s);
+    e = cudaMallocAsync(&d_table, table_bytes, s);
+    if (e != cudaSuccess) {
+        if (params_f) cudaFreeAsync(params_f, s);
+        return fail(SSA_ECUDA, std::string("group table: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(d_table, table.data(), table_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&counter, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
@@ -794,6 +829,7 @@ int simulate_multi_impl(int32_t n_groups, const ssa_group *groups, const ssa_opt
     // before cudaMemcpyAsync returned and `table` may go out of scope
     if (counter) cudaFreeAsync(counter, s);
     if (d_table) cudaFreeAsync(d_table, s);
+    if (params_f) cudaFreeAsync(params_f, s);
     if (e != cudaSuccess) return fail(SSA_ECUDA, std::string("multi launch: ") + cudaGetErrorString(e));
     return SSA_OK;
 }

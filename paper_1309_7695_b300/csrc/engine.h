@@ -44,6 +44,7 @@ struct GroupArgs {
     ModelLayout L;
     const int32_t *blob;
     const double *params;
+    const float *params_f;   // fast mode: the FP32 images of params, or null (converted on use)
     const int32_t *x0;
     const double *T;
     int32_t S;
@@ -73,6 +74,7 @@ struct SimArgs {
     ModelLayout L;
     const int32_t *blob;
     const double *params;
+    const float *params_f;   // fast mode: the FP32 images of params, or null (converted on use)
     const int32_t *x0;
     const double *T;
     int32_t S;
@@ -135,6 +137,8 @@ int lane_ref_occupancy(int block_warps, size_t smem, int reg_cap);
 // Fast-mode instantiation (kernel_lane_fast.cu), same shared-memory layout.
 cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s);
 int lane_fast_occupancy(int block_warps, size_t smem, int reg_cap);
+// FP32 images (round to nearest) of n rate constants, for fast mode.
+cudaError_t launch_params_to_f32(const double *in, float *out, long long n, cudaStream_t s);
 // Multi-network persistent instantiations (model read from global memory;
 // workspace sized for the largest network, no model staged in shared memory).
 size_t lane_multi_smem_bytes(int max_N, int max_M, int block_warps);

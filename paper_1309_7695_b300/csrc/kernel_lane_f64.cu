@@ -9,6 +9,8 @@ namespace tl {
 namespace {
 
 struct RefArith {
+    // slot sums in FP64, in the canonical order (no FP32 path)
+    static constexpr bool kFloatSlots = false;
     __device__ static __forceinline__ double prop(int info, double c, const int *X, int stride, int col)
     {
         return propensity_col(info, c, X, stride, col);

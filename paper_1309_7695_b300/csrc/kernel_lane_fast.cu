@@ -7,6 +7,8 @@
 // tau' (mu_i, sigma_i^2, the bounds and their minimum), as the reference
 // mode.  Counts stay exact integers.  Random numbers come from the same
 // Philox words as the reference mode, so the two modes are coupled.
+#include <algorithm>
+
 #include "device_fast.cuh"
 #include "lane_kernel.cuh"
 
@@ -14,18 +16,25 @@ namespace tl {
 namespace {
 
 struct FastArith {
-    // Conversions go through fast::f32_to_f64 / f64_to_f32 (integer pipe).
-    __device__ static __forceinline__ double prop(int info, double c, const int *X, int stride, int col)
+    // The SSA step sums each slot's propensities in FP32 and promotes the
+    // slot sum to FP64 for the tree (a0 and its partial sums stay FP64).
+    static constexpr bool kFloatSlots = true;
+    // FP32 propensity from the FP32 rate constant (its RN image)
+    __device__ static __forceinline__ float prop_f(int info, float cf, const int *X, int stride, int col)
     {
         const int kind = info & 3;
         const int s0 = (info >> 2) & 0x7fff;
         const int s1 = (info >> 17) & 0x7fff;
-        const float cf = f64::f64_to_f32(c);
-        if (kind == 0) return f64::f32_to_f64(cf);
-        if (kind == 1) return f64::f32_to_f64(cf * (float)X[s0 * stride + col]);
-        if (kind == 2) return f64::f32_to_f64((cf * (float)X[s0 * stride + col]) * (float)X[s1 * stride + col]);
+        if (kind == 0) return cf;
+        if (kind == 1) return cf * (float)X[s0 * stride + col];
+        if (kind == 2) return (cf * (float)X[s0 * stride + col]) * (float)X[s1 * stride + col];
         const int xi = X[s0 * stride + col];
-        return f64::f32_to_f64(cf * (0.5f * ((float)xi * (float)(xi - 1))));
+        return cf * (0.5f * ((float)xi * (float)(xi - 1)));
+    }
+    // Conversions go through f64::f32_to_f64 / f64_to_f32 (integer pipe).
+    __device__ static __forceinline__ double prop(int info, double c, const int *X, int stride, int col)
+    {
+        return f64::f32_to_f64(prop_f(info, f64::f64_to_f32(c), X, stride, col));
     }
     __device__ static __forceinline__ void uniforms(uint64_t seed, uint32_t sim, uint32_t attempt, uint32_t purpose,
                                                     double &ua, double &ub)
@@ -78,7 +87,21 @@ struct FastArith {
     }
 };
 
+__global__ void params_to_f32(const double *__restrict__ in, float *__restrict__ out, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_params_to_f32(const double *in, float *out, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 148ll * 8);
+    params_to_f32<<<(int)blocks, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lane_fast(const SimArgs &a, int block_warps, int grid, size_t smem, int carveout, int reg_cap, cudaStream_t s)
 {

@@ -51,6 +51,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "device_f64.cuh"
 #include "engine.h"
@@ -61,6 +62,24 @@ namespace lane {
 
 constexpr int kStride = 33;
 constexpr int kNodes = 63;
+
+// Deferred SSA steps.  A lane-local SSA step is one pass of the warp whose
+// FP64 instructions cost the same issue time however many lanes take part, so
+// while some lanes still leap (their cooperative steps run every iteration
+// anyway) the pass is taken only when at least kGatherNum / kGatherDen of the
+// live lanes are in the SSA phase, or after kGatherWait iterations without
+// one.  Only the order in which a warp interleaves its simulations changes;
+// each simulation's arithmetic and random streams are its own, so results do
+// not.  kGatherNum = 0 takes the pass every iteration.
+#ifndef TL_SSA_GATHER_NUM
+#define TL_SSA_GATHER_NUM 0
+#endif
+#ifndef TL_SSA_GATHER_WAIT
+#define TL_SSA_GATHER_WAIT 8
+#endif
+constexpr int kGatherNum = TL_SSA_GATHER_NUM;
+constexpr int kGatherDen = 4;
+constexpr int kGatherWait = TL_SSA_GATHER_WAIT;
 enum : int { P_NEED = 0, P_TOP = 1, P_SSA = 2, P_DONE = 3, P_IDLE = 4 };
 
 __host__ __device__ constexpr int node_base(int k) { return 64 - (64 >> k); }
@@ -123,6 +142,7 @@ struct GroupView {
     int N, M, S;
     double t_end;
     const double *params;
+    const float *params_f;   // fast mode: FP32 images of params, or null
     const int32_t *x0;
     const double *T;
     int32_t *samples;
@@ -183,6 +203,7 @@ __device__ __forceinline__ GroupView view_single(const SimArgs &A, const int *sm
     G.S = A.S;
     G.t_end = A.t_end;
     G.params = A.params;
+    G.params_f = A.params_f;
     G.x0 = A.x0;
     G.T = A.T;
     G.samples = A.samples;
@@ -210,6 +231,7 @@ __device__ __forceinline__ GroupView view_group(const GroupArgs *groups, int g)
     G.S = R.S;
     G.t_end = R.t_end;
     G.params = R.params;
+    G.params_f = R.params_f;
     G.x0 = R.x0;
     G.T = R.T;
     G.samples = R.samples;
@@ -268,6 +290,7 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
     int phase = P_NEED;
     int ssa_left = 0;
     int first = 0;
+    int ssa_wait = 0;   // warp-uniform: consecutive iterations that deferred the SSA pass
     long long leaps = 0, rejected = 0, ssa_steps = 0, firings = 0;
     double tnext = kInf;   // T[ks], or +inf once every sample is recorded
     // warp-uniform: the (group, row) whose rate constants are in w.c
@@ -279,7 +302,15 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
     const float ssaf = f64::f64_to_f32(A.ssa_factor);
     const bool ssaf_ok = f64::nn_ge(1e30, A.ssa_factor);
 
+    // FP32 rate constant of this lane's simulation (fast mode): the staged
+    // image, or the RN conversion of the FP64 constant (the same value)
+    auto own_cf = [&](const GroupView &G, int j) -> float {
+        return G.params_f ? __ldg(G.params_f + (size_t)row * G.M + j)
+                          : f64::f64_to_f32(__ldg(G.params + (size_t)row * G.M + j));
+    };
     auto own_prop = [&](const GroupView &G, int j) -> double {
+        if constexpr (Arith::kFloatSlots)
+            return f64::f32_to_f64(Arith::prop_f(G.rinfo[j], own_cf(G, j), X, kStride, lane));
         return Arith::prop(G.rinfo[j], __ldg(G.params + (size_t)row * G.M + j), X, kStride, lane);
     };
     // Slot sum of this lane's simulation, S_l = sum over j = l, l+32, ... of
@@ -287,8 +318,14 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
     // slot (M <= 128) their rate constants are loaded together before the
     // first is used, so the global-memory latency is paid once per slot.
     auto own_slot_sum = [&](const GroupView &G, int l) -> double {
-        const double *c = G.params + (size_t)row * G.M;
         const int M = G.M;
+        if constexpr (Arith::kFloatSlots) {
+            // fast mode: the slot's FP32 propensities summed in FP32, promoted once
+            float sf = Arith::prop_f(G.rinfo[l], own_cf(G, l), X, kStride, lane);
+            for (int j = l + 32; j < M; j += 32) sf = sf + Arith::prop_f(G.rinfo[j], own_cf(G, j), X, kStride, lane);
+            return f64::first_term(f64::f32_to_f64(sf));
+        }
+        const double *c = G.params + (size_t)row * G.M;
         if (M <= 128) {
             const double c0 = __ldg(c + l);
             const double c1 = (l + 32 < M) ? __ldg(c + l + 32) : 0.0;
@@ -303,6 +340,25 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
         double s = f64::first_term(own_prop(G, l));
         for (int j = l + 32; j < M; j += 32) s = s + own_prop(G, j);
         return s;
+    };
+    // The SSA step's propensity arithmetic: FP64 in the reference mode, FP32
+    // (with FP32 rate constants, and slot sums promoted to FP64 once) in fast mode
+    using acc_t = typename std::conditional<Arith::kFloatSlots, float, double>::type;
+    auto load_c = [&](const GroupView &G, int j) -> acc_t {
+        if constexpr (Arith::kFloatSlots) return own_cf(G, j);
+        else return __ldg(G.params + (size_t)row * G.M + j);
+    };
+    auto prop_c = [&](int info, acc_t c) -> acc_t {
+        if constexpr (Arith::kFloatSlots) return Arith::prop_f(info, c, X, kStride, lane);
+        else return Arith::prop(info, c, X, kStride, lane);
+    };
+    auto to_f64 = [](acc_t v) -> double {
+        if constexpr (Arith::kFloatSlots) return f64::f32_to_f64(v);
+        else return v;
+    };
+    auto first_acc = [](acc_t v) -> acc_t {   // +0 + v: the sign of a zero cleared
+        if constexpr (Arith::kFloatSlots) return __int_as_float(__float_as_int(v) & 0x7fffffff);
+        else return f64::first_term(v);
     };
     auto lane_record = [&](const GroupView &G, int k) {
         for (int i = 0; i < G.N; ++i) record_count(G, row, k, i, X[i * kStride + lane]);
@@ -567,9 +623,11 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                             for (int e = tr_ptr[i]; e < tr_ptr[i + 1]; ++e) {
                                 const int ent = tr_ent[e];
                                 const int j = ent >> 8;
-                                if (w.crit[j]) continue;
+                                // af[j] is 0 exactly when j is critical or a_j is not positive
+                                // (an out-of-range a_j has a NaN image): the canonical terms
+                                const float af = w.af[j];
                                 const double a = w.a[j];
-                                if (!f64::nn_pos(a)) continue;
+                                if (af == 0.0f) continue;
                                 const int nv = (signed char)(ent & 0xff);
                                 // nu a and nu^2 a: for |nu| <= 2 exact power-of-two scalings and a
                                 // sign flip (exponent arithmetic on a > 0, normal, far from
@@ -877,8 +935,22 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
             }
         }
 
-        // ---- lane-local part: one exact SSA step (direct method)
-        if (phase == P_SSA) {
+        // ---- lane-local part: one exact SSA step (direct method), unless deferred
+        bool ssa_go = (phase == P_SSA);
+        if (kGatherNum > 0 && !exact) {
+            const unsigned b_ssa = __ballot_sync(kFull, phase == P_SSA);
+            if (b_ssa) {
+                const unsigned b_lead = __ballot_sync(kFull, phase == P_TOP || phase == P_DONE);
+                const unsigned b_live = __ballot_sync(kFull, phase != P_IDLE);
+                if (b_lead && kGatherDen * __popc(b_ssa) < kGatherNum * __popc(b_live) && ssa_wait < kGatherWait) {
+                    ++ssa_wait;
+                    ssa_go = false;
+                } else {
+                    ssa_wait = 0;
+                }
+            }
+        }
+        if (ssa_go) {
             const GroupView G = gview(grp);
             const int *nu_ptr = G.nu_ptr, *nu_ent = G.nu_ent;
             const int M = G.M, S = G.S;
@@ -929,19 +1001,18 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                                 cls += step;
                             }
                         }
-                        double cum = 0.0;
+                        acc_t cum = 0;
                         int jf = -1, last = -1;
                         // walk the slot; the next member's rate constant is loaded one step ahead
-                        const double *cp = G.params + (size_t)row * M;
-                        double cnext = __ldg(cp + cls);
+                        acc_t cnext = load_c(G, cls);
                         for (int j = cls; j < M; j += 32) {
-                            const double cj = cnext;
-                            if (j + 32 < M) cnext = __ldg(cp + j + 32);
-                            const double v = Arith::prop(G.rinfo[j], cj, X, kStride, lane);
-                            if (j == cls) cum = f64::first_term(v);
+                            const acc_t cj = cnext;
+                            if (j + 32 < M) cnext = load_c(G, j + 32);
+                            const acc_t v = prop_c(G.rinfo[j], cj);
+                            if (j == cls) cum = first_acc(v);
                             else cum = cum + v;
-                            if (f64::nn_pos(v)) last = j;
-                            if (f64::nn_gt(cum, target)) {
+                            if (f64::nn_pos(to_f64(v))) last = j;
+                            if (f64::nn_gt(to_f64(cum), target)) {
                                 jf = j;
                                 break;
                             }
@@ -972,27 +1043,26 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                                 // loaded while the current slot is summed
                                 unsigned m = dirty;
                                 if (m != 0 && M <= 128) {
-                                    const double *cp = G.params + (size_t)row * M;
                                     int l = __ffs(m) - 1;
                                     m &= m - 1;
-                                    double c0 = __ldg(cp + l), c1 = (l + 32 < M) ? __ldg(cp + l + 32) : 0.0;
-                                    double c2 = (l + 64 < M) ? __ldg(cp + l + 64) : 0.0;
-                                    double c3 = (l + 96 < M) ? __ldg(cp + l + 96) : 0.0;
+                                    acc_t c0 = load_c(G, l), c1 = (l + 32 < M) ? load_c(G, l + 32) : acc_t(0);
+                                    acc_t c2 = (l + 64 < M) ? load_c(G, l + 64) : acc_t(0);
+                                    acc_t c3 = (l + 96 < M) ? load_c(G, l + 96) : acc_t(0);
                                     for (;;) {
                                         const int ln = m ? __ffs(m) - 1 : -1;
                                         m &= m - 1;
-                                        double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
+                                        acc_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
                                         if (ln >= 0) {
-                                            n0 = __ldg(cp + ln);
-                                            if (ln + 32 < M) n1 = __ldg(cp + ln + 32);
-                                            if (ln + 64 < M) n2 = __ldg(cp + ln + 64);
-                                            if (ln + 96 < M) n3 = __ldg(cp + ln + 96);
+                                            n0 = load_c(G, ln);
+                                            if (ln + 32 < M) n1 = load_c(G, ln + 32);
+                                            if (ln + 64 < M) n2 = load_c(G, ln + 64);
+                                            if (ln + 96 < M) n3 = load_c(G, ln + 96);
                                         }
-                                        double sl = f64::first_term(Arith::prop(G.rinfo[l], c0, X, kStride, lane));
-                                        if (l + 32 < M) sl = sl + Arith::prop(G.rinfo[l + 32], c1, X, kStride, lane);
-                                        if (l + 64 < M) sl = sl + Arith::prop(G.rinfo[l + 64], c2, X, kStride, lane);
-                                        if (l + 96 < M) sl = sl + Arith::prop(G.rinfo[l + 96], c3, X, kStride, lane);
-                                        V[l * kStride + lane] = sl;
+                                        acc_t sl = first_acc(prop_c(G.rinfo[l], c0));
+                                        if (l + 32 < M) sl = sl + prop_c(G.rinfo[l + 32], c1);
+                                        if (l + 64 < M) sl = sl + prop_c(G.rinfo[l + 64], c2);
+                                        if (l + 96 < M) sl = sl + prop_c(G.rinfo[l + 96], c3);
+                                        V[l * kStride + lane] = to_f64(sl);
                                         if (ln < 0) break;
                                         l = ln;
                                         c0 = n0;
