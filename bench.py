@@ -22,6 +22,12 @@ simulation kernel against the FP64 issue rate, and the CPU oracle on a
 bounded sample of the same workload (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+
+Other workloads (--workload): rand128x256 (the 128 x 256 sweep, 16,384
+parameter sets to t_end = 100, FP64 and fast mode), hetero (uneven groups of
+8 networks in one autotuned persistent launch against one launch per
+network), served (a Poisson request stream through the server), rre (batched
+rate-equation integration) and cle (the Langevin leap).
 Multi-GPU (torchrun, one rank per GPU): each rank simulates its own 65,536
 simulations (global indices rank*65536 + r), so per-GPU work is fixed
 (weak scaling) and no collective is needed on the data path.
@@ -319,6 +325,55 @@ def run_hetero(args):
     return 0
 
 
+def run_sweep128(args):
+    """The 128 x 256 sweep at its full size and horizon: 16,384 parameter
+    sets (initial counts up to 10^4), t_end = 100, 101 sample times, attempt
+    cap 2^20, one launch in FP64 reference mode (the launch the digest test
+    compares with the oracle) and one in fast mode, L2 flushed before each."""
+    import torch
+
+    from paper_1309_7695_b300 import abi
+
+    dev = torch.device("cuda:0")
+    cap = 1 << 20
+    b = inputs.random_batch(128, 256, 16384, seed=0, x0_max=10_000, t_end=100.0, n_samples=101)
+    n, N, S = b.n_sims, b.network.n_species, len(b.sample_times)
+    model = abi.Model(b.network)
+    p = torch.from_numpy(b.params).to(dev)
+    x = torch.from_numpy(b.x0).to(dev)
+    T = torch.from_numpy(b.sample_times).to(dev)
+    out = torch.empty((n, S, N), dtype=torch.int32, device=dev)
+    st = torch.empty((n, abi.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    legs = {}
+    for name, prec in (("fp64", abi.SSA_FP64_REF), ("fast", abi.SSA_FAST)):
+        o = abi.ssa_default_options(precision=prec, max_attempts=cap)
+        flush.fill_(7)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        abi.ssa_simulate_dev(model, p, x, b.t_end, T, out, st, seed=0, opts=o)
+        e1.record()
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        s = st.cpu().numpy().view(abi.STATS_DTYPE).reshape(n)
+        fir = float(s["firings"].astype(np.float64).sum())
+        steps = float(s["leaps"].astype(np.float64).sum() + s["ssa_steps"].astype(np.float64).sum())
+        legs[name] = {"seconds": dt, "firings_per_s": fir / dt, "sim_steps_per_s": steps / dt,
+                      "firings": fir, "capped_fraction": float((s["status"] == abi.SSA_STATUS_STEP_LIMIT).mean()),
+                      "ssa_step_fraction": float(s["ssa_steps"].astype(np.float64).sum()) / steps}
+    model.close()
+    line = {"metric": METRIC, "workload": "rand128x256", "value": legs["fast"]["firings_per_s"], "unit": "firings/s",
+            "sim_steps_per_s": legs["fast"]["sim_steps_per_s"], "fp64": legs["fp64"], "fast": legs["fast"],
+            "fast_vs_fp64": legs["fast"]["firings_per_s"] / legs["fp64"]["firings_per_s"],
+            "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'", "data": "synthetic",
+            "config": {"workload": "random 128 x 256 network (orders 0/1/2 in 1:2:1), 16,384 parameter sets, "
+                                   "x0 U-int[0,10^4], t_end=100, 101 sample times, eps=0.03, n_c=10",
+                       "max_attempts": cap, "schedule": "one launch per mode, default shape, L2 flushed before each"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def served_stream(rates, n_requests, n_networks, cap, seed=7, n_streams=4, max_batch=16):
     """Served request stream (continuous batching through abi.Server): a pool
     of random networks (M logU-int[8,512], N U-int[4,min(256,2M)]); per
@@ -593,7 +648,7 @@ def main():
     # profiling / sweep knobs; the reported benchmark uses the defaults
     ap.add_argument("--sims", type=int, default=None, help="override the simulations per GPU (profiling)")
     ap.add_argument("--cap", type=int, default=None, help="override the per-simulation attempt cap (profiling)")
-    ap.add_argument("--workload", default="rand32x64", choices=["rand32x64", "hetero", "served", "rre", "cle"])
+    ap.add_argument("--workload", default="rand32x64", choices=["rand32x64", "rand128x256", "hetero", "served", "rre", "cle"])
     ap.add_argument("--rre-sims", type=int, default=4096)
     ap.add_argument("--rre-t-end", type=float, default=10.0)
     ap.add_argument("--rre-samples", type=int, default=11)
@@ -613,6 +668,8 @@ def main():
         return run_reference(args)
     if args.workload == "hetero":
         return run_hetero(args)
+    if args.workload == "rand128x256":
+        return run_sweep128(args)
     if args.workload == "served":
         return run_served(args)
     if args.workload == "rre":
