@@ -54,12 +54,29 @@ METRIC = "reaction firings/s & sim-steps/s (KS-matched) vs plain FP64; serve p50
 WORKLOAD = dict(n_species=32, n_reactions=64, n_sims=65536, t_end=100.0, n_samples=101,
                 x0_max=1000, eps=0.03, n_c=10, max_attempts=1 << 20, network_seed=0)
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes per simulation of the persistent lane kernels: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu-captured launch of 65,536 simulations of the
+# workload above at an attempt cap of 2^16, divided by 65,536.  The bytes are the
+# inputs read and the samples written, so they scale with the simulations a launch
+# runs and not with its attempts.
+TRAFFIC_BYTES_PER_SIM = {"RefArith": 14250.0, "FastArith": 14398.5}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of 65,536 simulations "
+                  "(attempt cap 2^16), scaled by the simulations of this launch")
 def kernel_name(args):
     """The simulation kernel a headline launch runs."""
     if args.layout == 1:
         return "warp_f64_kernel"
     arith = "RefArith" if args.precision == "fp64" else "FastArith"
     return f"lane_kernel<{arith}, {'true' if args.schedule == 'multi' else 'false'}>"
+
+
+def traffic_per_launch(args, precision, n_sims):
+    """DRAM bytes of one headline launch of the lane kernel (None for the warp layout, which
+    has no capture): the measured bytes per simulation times the simulations it runs."""
+    if args.layout == 1:
+        return None
+    per_launch = n_sims * (args.steps if args.schedule == "multi" else 1)
+    return TRAFFIC_BYTES_PER_SIM["RefArith" if precision == "fp64" else "FastArith"] * per_launch
 
 
 def propensity_ops(net):
@@ -841,7 +858,9 @@ def main():
                            "vs_plain_fp64": (mf / mt) / plain["value"] if plain else None,
                            "roofline": {"bound": "alu", "achieved": mops / mt / 1e12, "peak": peak_ops / 1e12,
                                         "unit": "T FP64-op/s (method ops at FP64 rate)",
-                                        "frac": mops / mt / peak_ops, "peak_source": "of measured (live)"},
+                                        "frac": mops / mt / peak_ops, "peak_source": "of measured (live)",
+                                        "traffic": TRAFFIC_BYTES_PER_SIM["FastArith"] * side_k * n,
+                                        "traffic_source": TRAFFIC_SOURCE},
                            "dtype": "f32 propensities/Poisson, f64 clock/a0/tau'"}
 
     moments = None
@@ -916,7 +935,8 @@ def main():
                                              "L2 flushed before the timed region"}),
                 "roofline": None if args.no_work_counters else {
                              "bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                             "unit": "T FP64-op/s", "frac": achieved / peak_ops, "traffic": None,
+                             "unit": "T FP64-op/s", "frac": achieved / peak_ops,
+                             "traffic": traffic_per_launch(args, args.precision, n), "traffic_source": TRAFFIC_SOURCE,
                              "kernel": kernel_name(args),
                              "peak_source": "of measured: FP64 add rate of this device, measured live by "
                                             "ssa_measure_issue_rates",
