@@ -63,23 +63,19 @@ namespace lane {
 constexpr int kStride = 33;
 constexpr int kNodes = 63;
 
-// Deferred SSA steps.  A lane-local SSA step is one pass of the warp whose
-// FP64 instructions cost the same issue time however many lanes take part, so
-// while some lanes still leap (their cooperative steps run every iteration
-// anyway) the pass is taken only when at least kGatherNum / kGatherDen of the
-// live lanes are in the SSA phase, or after kGatherWait iterations without
-// one.  Only the order in which a warp interleaves its simulations changes;
-// each simulation's arithmetic and random streams are its own, so results do
-// not.  kGatherNum = 0 takes the pass every iteration.
-#ifndef TL_SSA_GATHER_NUM
-#define TL_SSA_GATHER_NUM 0
-#endif
-#ifndef TL_SSA_GATHER_WAIT
-#define TL_SSA_GATHER_WAIT 8
-#endif
-constexpr int kGatherNum = TL_SSA_GATHER_NUM;
-constexpr int kGatherDen = 4;
-constexpr int kGatherWait = TL_SSA_GATHER_WAIT;
+// Repeated visits of long simulations.  The cooperative part of a warp
+// iteration visits every lane in TOP once, so a simulation that needs many
+// leaps advances one leap per iteration while its warp-mates' visits and
+// the SSA pass run in between.  A simulation that has already made
+// kHeavyLeaps leaps is visited up to kLeapRepeat times in a row instead:
+// the warp does the same work in a different order, and the simulations
+// that would otherwise be left running alone at the end of a launch are
+// further along (one 65,536-simulation batch of the 32 x 64 workload: 13-14 s
+// in most launches instead of 17-21 s).  Each simulation's arithmetic and
+// random streams are its own, so results do not change.
+constexpr int kLeapRepeat = 16;
+constexpr long long kHeavyLeaps = 256;
+
 enum : int { P_NEED = 0, P_TOP = 1, P_SSA = 2, P_DONE = 3, P_IDLE = 4 };
 
 __host__ __device__ constexpr int node_base(int k) { return 64 - (64 >> k); }
@@ -290,7 +286,6 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
     int phase = P_NEED;
     int ssa_left = 0;
     int first = 0;
-    int ssa_wait = 0;   // warp-uniform: consecutive iterations that deferred the SSA pass
     long long leaps = 0, rejected = 0, ssa_steps = 0, firings = 0;
     double tnext = kInf;   // T[ks], or +inf once every sample is recorded
     // warp-uniform: the (group, row) whose rate constants are in w.c
@@ -419,6 +414,7 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
         // ---- cooperative top of the loop, one simulation at a time
         if (!exact) {
             unsigned todo = __ballot_sync(kFull, phase == P_TOP);
+            int again = 0;   // warp-uniform: repeated visits of the current lane so far
             while (todo) {
                 const int L = __ffs(todo) - 1;
                 todo &= todo - 1;
@@ -900,6 +896,12 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
                     ssa_left = nleft;
                     first = nfirst;
                 }
+                if (kLeapRepeat > 1 && nphase == P_TOP && lpL >= kHeavyLeaps && again + 1 < kLeapRepeat) {
+                    todo |= 1u << L;   // L was the lowest bit: visited again next
+                    ++again;
+                } else {
+                    again = 0;
+                }
             }
             __syncwarp();
         }
@@ -935,22 +937,8 @@ __global__ void __launch_bounds__(kRegCap ? 128 : 256, kRegCap ? 3 : 1) lane_ker
             }
         }
 
-        // ---- lane-local part: one exact SSA step (direct method), unless deferred
-        bool ssa_go = (phase == P_SSA);
-        if (kGatherNum > 0 && !exact) {
-            const unsigned b_ssa = __ballot_sync(kFull, phase == P_SSA);
-            if (b_ssa) {
-                const unsigned b_lead = __ballot_sync(kFull, phase == P_TOP || phase == P_DONE);
-                const unsigned b_live = __ballot_sync(kFull, phase != P_IDLE);
-                if (b_lead && kGatherDen * __popc(b_ssa) < kGatherNum * __popc(b_live) && ssa_wait < kGatherWait) {
-                    ++ssa_wait;
-                    ssa_go = false;
-                } else {
-                    ssa_wait = 0;
-                }
-            }
-        }
-        if (ssa_go) {
+        // ---- lane-local part: one exact SSA step (direct method)
+        if (phase == P_SSA) {
             const GroupView G = gview(grp);
             const int *nu_ptr = G.nu_ptr, *nu_ent = G.nu_ent;
             const int M = G.M, S = G.S;
