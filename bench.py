@@ -59,7 +59,7 @@ L2_FLUSH_BYTES = 256 << 20
 # workload above at an attempt cap of 2^16, divided by 65,536.  The bytes are the
 # inputs read and the samples written, so they scale with the simulations a launch
 # runs and not with its attempts.
-TRAFFIC_BYTES_PER_SIM = {"RefArith": 14250.0, "FastArith": 14398.5}
+TRAFFIC_BYTES_PER_SIM = {"RefArith": 14291.1, "FastArith": 14339.2}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of 65,536 simulations "
                   "(attempt cap 2^16), scaled by the simulations of this launch")
 def kernel_name(args):
