@@ -70,9 +70,10 @@ constexpr int kNodes = 63;
 // kHeavyLeaps leaps is visited up to kLeapRepeat times in a row instead:
 // the warp does the same work in a different order, and the simulations
 // that would otherwise be left running alone at the end of a launch are
-// further along (one 65,536-simulation batch of the 32 x 64 workload: 13-14 s
-// in most launches instead of 17-21 s).  Each simulation's arithmetic and
-// random streams are its own, so results do not change.
+// further along (one 65,536-simulation batch of the 32 x 64 workload:
+// 13-20 s, median about 15 s over 12 launches, instead of 17-21 s).  Each
+// simulation's arithmetic and random streams are its own, so results do
+// not change.
 constexpr int kLeapRepeat = 16;
 constexpr long long kHeavyLeaps = 256;
 
