@@ -181,7 +181,9 @@ int ssa_model_info(ssa_model_t model, int32_t *n_species, int32_t *n_reactions);
  * Simulation r uses the random stream of global index sim_offset + r
  * (sim_offset + n_sims <= 2^32).  Returns as soon as the launch is queued;
  * the function allocates a small stream-ordered work counter and frees it
- * on the same stream.  The first launch on each device also copies the
+ * on the same stream; in fast mode (lane layout) it also allocates the FP32
+ * images of params (4 * n_sims * M bytes), forms them with a conversion
+ * kernel on `stream` and frees them there.  The first launch on each device also copies the
  * logarithm table (6 KB, built on the host) into device memory on `stream`
  * and waits for that copy, so make one launch on a device before capturing
  * launches into a CUDA graph.  The library keeps per-device state for the
@@ -256,7 +258,9 @@ int ssa_integrate_rre_dev(ssa_model_t model, int64_t n_sims, const double *param
 /* Same as ssa_simulate_dev, for callers that cannot allocate device memory
  * (for example code that runs inside an allocator's callbacks, or programs
  * that reserve all device memory up front).  It calls no cudaMalloc,
- * cudaFree or other allocating routine.  The one piece of scratch memory the
+ * cudaFree or other allocating routine; in fast mode the kernel converts
+ * each rate constant to FP32 where it uses it (the same values as the
+ * staged images of ssa_simulate_dev).  The one piece of scratch memory the
  * kernel needs, its 8-byte work counter, lives in a 256-byte static device
  * array that every GPU loading this library keeps until process exit; a
  * launch needing more scratch than that is rejected with SSA_EINVAL.  Each
