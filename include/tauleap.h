@@ -304,7 +304,8 @@ typedef struct {
  * simulation are identical to ssa_simulate_dev of its group with the same
  * options and seed.  opts->precision applies to every group; the lane
  * layout is used.  Allocates (stream-ordered) the group table and the work
- * counter and frees them on `stream`. */
+ * counter, in fast mode also the FP32 images of every group's params, and
+ * frees them on `stream`. */
 int ssa_simulate_multi_dev(int32_t n_groups, const ssa_group *groups, const ssa_options *opts, void *stream);
 
 /* Host-buffer form.  Copies the HOST inputs to device memory that the job
