@@ -70,6 +70,13 @@ def kernel_name(args):
     return f"lane_kernel<{arith}, {'true' if args.schedule == 'multi' else 'false'}>"
 
 
+def ordinal(k):
+    """1st, 2nd, 3rd, 4th, ..., 32nd: for the sample descriptions."""
+    if 10 <= k % 100 <= 20:
+        return f"{k}th"
+    return f"{k}" + {1: "st", 2: "nd", 3: "rd"}.get(k % 10, "th")
+
+
 def traffic_per_launch(args, precision, n_sims):
     """DRAM bytes of one headline launch of the lane kernel (None for the warp layout, which
     has no capture): the measured bytes per simulation times the simulations it runs."""
@@ -229,10 +236,10 @@ def cpu_oracle_rate(batch, n_sample=2048, seed=1000, gpu_stats=None):
     fa, sa, da = timed(rows1, cores)   # the same simulations on all cores (restores the thread count)
     one_core = {"value": f1, "unit": "firings/s", "sim_steps_per_s": s1, "cores": 1, "seconds": round(d1, 2),
                 "all_cores_same_sample": fa, "speedup_all_cores": d1 / da,
-                "sample": f"every {stride * 8}th simulation ({len(rows1)} simulations)"}
+                "sample": f"every {ordinal(stride * 8)} simulation ({len(rows1)} simulations)"}
     return {"value": fir, "unit": "firings/s", "sim_steps_per_s": steps,
             "cores": cores, "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"every {stride}th of the {batch.n_sims} simulations ({len(rows)} simulations, "
+            "sample": f"every {ordinal(stride)} of the {batch.n_sims} simulations ({len(rows)} simulations, "
                       f"seed {seed}), OpenMP over simulations", "one_core": one_core, "mix": mix,
             "heaviest": heavy}
 
@@ -263,9 +270,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded random network and sweep)", "sim_steps_per_s": steps / dt,
-            "config": config_dict({"reference_sample": f"{per_step} simulations per step (every {stride}th)"}),
+            "config": config_dict({"reference_sample": f"{per_step} simulations per step (every {ordinal(stride)})"}),
             "cpu_baseline": {"value": value, "unit": "firings/s", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"every {stride}th of {batch.n_sims} simulations ({per_step}) per step"},
+                             "sample": f"every {ordinal(stride)} of {batch.n_sims} simulations ({per_step}) per step"},
             "e2e": {"value": value, "unit": "firings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
