@@ -891,6 +891,8 @@ def main():
         mf = sum(float(sts[k].cpu().numpy().view(abi.STATS_DTYPE)["firings"].sum()) for k in range(side_k))
         mt, (mf,) = shard.reduce_run(mt, [mf], device=dev)
         moments = {"value": mf / mt, "unit": "firings/s", "ms_per_step": mt * 1e3 / side_k, "batches": side_k,
+                   "schedule": f"one launch per batch on its own stream ({side_k} streams), not the headline's "
+                               "persistent launch",
                    "output_bytes_per_step": int(2 * S * N * 8), "trajectory_bytes_per_step": int(n * S * N * 4)}
 
     e2e = None
