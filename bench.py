@@ -822,7 +822,7 @@ def main():
     capped = sum(int((s["status"] == abi.SSA_STATUS_STEP_LIMIT).sum()) for s in stats)
     t_max, (fir, simsteps, ops, capped) = shard.reduce_run(local_t, [fir, simsteps, ops, capped], device=dev)
 
-    # ---- the spec comparison: the plain one-launch-per-batch FP64 kernel against the
+    # ---- the target comparison: the plain one-launch-per-batch FP64 kernel against the
     # fast form in one persistent launch (the fast form's accuracy against FP64: the coupled
     # KS / moment tests)
     plain = None
